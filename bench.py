@@ -1,0 +1,461 @@
+#!/usr/bin/env python3
+"""Benchmark: forward + backward trilinear point splatting on GB300.
+
+Workload (default): 6M-point scene-shaped cloud (noisy heightfield ground,
+Gaussian clusters, far shell; Pareto sizes) rendered at 1920x1080 into 8
+pyramid layers, K = 16, D = 4 float32 descriptors, kept lists recomputed in
+the backward pass.  One step = project -> splat -> blend -> backward for one
+frame with a fixed upstream gradient.  Inputs are resident in HBM when the
+timed region starts; the point inputs alone (216 MB) are larger than L2.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the float64 CPU
+oracle on the host cores instead (a bounded random subset of the same cloud
+per step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd ms/frame & Mpoints/s, 6M pts @1080p; % of HBM roofline"
+FALLBACK_HBM_GBS = 6800.0
+KERNELS_PER_STEP = 5  # k_project_count, k_scan_tiles, k_fill, k_tile_blend, k_tile_backward
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="ground6m_1080p")
+    ap.add_argument("--mode", choices=["recompute", "store"], default="recompute")
+    ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--ref-sample", type=int, default=2_000_000, help="points per reference-arm step")
+    ap.add_argument("--cpu-frames", type=int, default=2, help="full oracle frames timed for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only: every rank renders its own frame)
+# ---------------------------------------------------------------------------
+
+def dist_setup(use_cuda):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl" if use_cuda else "gloo")
+    if use_cuda:
+        torch.cuda.set_device(local)
+    return rank, world, local
+
+
+def barrier(world, device=None):
+    import torch.distributed as dist
+
+    if world > 1:
+        if device is not None:
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+def max_over_ranks(x, world, device):
+    import torch
+    import torch.distributed as dist
+
+    if world == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = max(smax, float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping
+# ---------------------------------------------------------------------------
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            v = float(json.load(fh)["hbm_gbs"])
+        return v, "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2401_06003_gb300", "csrc", "*"))):
+        with open(p, "rb") as fh:
+            h.update(os.path.basename(p).encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken from the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if d.get("source_hash") != source_hash():
+        return None
+    k = d.get("kernels", {}).get(kernel)
+    if not k or k.get("workload") != workload:
+        return None
+    return k.get("dram_bytes_per_launch")
+
+
+def algorithmic_bytes(N, V, F, P, D, b):
+    """Per-stage algorithmic bytes of one frame (per launch).
+
+    project  : read x, s_w, alpha (20 N) + write the point record (16 V)
+    splat    : write each fragment key once (8 F) + the pixel offsets (8 P)
+    blend    : read each key once (8 F) + descriptors (b D V) + write the pyramid (4 D P)
+    backward : re-read keys (8 F), records and descriptors ((16 + b D) V),
+               read dL/dpyramid (4 D P), write the gradients (4 (5 + D) N)
+    The first three sum to the forward total 20N + (16 + bD)V + 16F + 8P + 4DP.
+    """
+    return {
+        "project": 20 * N + 16 * V,
+        "splat": 8 * F + 8 * P,
+        "blend": 8 * F + b * D * V + 4 * D * P,
+        "backward": 8 * F + (16 + b * D) * V + 4 * D * P + 4 * (5 + D) * N,
+    }
+
+
+# ---------------------------------------------------------------------------
+# the CUDA path
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+
+    from paper_2401_06003_gb300 import Renderer, scenes
+    from paper_2401_06003_gb300.build import build as build_lib
+
+    build_lib()
+    rank, world, local = dist_setup(True)
+    dev = torch.device("cuda", local)
+    sc = scenes.make_config(args.workload)
+    tw, th = (int(v) for v in args.tile.split("x"))
+    desc_dtype = torch.bfloat16 if args.workload.endswith("bf16") else torch.float32
+    r = Renderer(sc.camera, sc.n_layers, K=sc.K, D=sc.D, desc_dtype=desc_dtype, mode=args.mode, tile=(tw, th),
+                 device=dev)
+    N, D, P = sc.n, sc.D, r.P
+    b = 2 if desc_dtype == torch.bfloat16 else 4
+
+    pos = torch.from_numpy(sc.pos).to(dev)
+    sw = torch.from_numpy(sc.size_w).to(dev)
+    op = torch.from_numpy(sc.opacity).to(dev)
+    desc = torch.from_numpy(sc.desc).to(dev).to(desc_dtype).contiguous()
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1234 + rank)
+    G = (torch.rand((P, D), generator=gen, device=dev) * 2 - 1).contiguous()
+    ws = r.new_workspace(N)
+    rec = torch.empty((N, 4), dtype=torch.float32, device=dev)
+    pyr = torch.empty((P, D), dtype=torch.float32, device=dev)
+    grads = (torch.empty((N, 3), device=dev), torch.empty((N,), device=dev), torch.empty((N,), device=dev),
+             torch.empty((N, D), device=dev))
+    store = args.mode == "store"
+    stream = torch.cuda.current_stream(dev)
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        r.project(pos, sw, ws, records=rec)
+        if ev is not None:
+            ev[1].record(stream)
+        r.splat_forward(rec, ws)
+        if ev is not None:
+            ev[2].record(stream)
+        _, kept, nk, _, _ = r.blend(rec, op, desc, ws, store_lists=store, pyramid=pyr)
+        if ev is not None:
+            ev[3].record(stream)
+        r.splat_backward(rec, op, desc, G, ws, kept if store else None, nk if store else None, grads=grads)
+        if ev is not None:
+            ev[4].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    flags = r.status(ws)
+    if flags:
+        raise RuntimeError(f"device status flags {flags:#x} after warm-up")
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    clocks = ClockSampler(torch.cuda.current_device()) if not args.no_clocks else None
+    barrier(world, dev)
+    torch.cuda.synchronize(dev)
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for s in range(args.steps):
+        step(evs[s])
+    t1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world, dev)
+    clk = clocks.stop() if clocks else None
+    elapsed_ms = max_over_ranks(t0.elapsed_time(t1), world, dev)
+    stage_ms = {name: float(np.mean([evs[s][q].elapsed_time(evs[s][q + 1]) for s in range(args.steps)]))
+                for q, name in enumerate(["project", "splat", "blend", "backward"])}
+
+    # counters of the frame (untimed)
+    _, kept, nk, tfin, nfrag = r.blend(rec, op, desc, ws, stats=True)
+    V = int((rec[:, 2] > 0).sum().item())
+    F = int(nfrag.to(torch.int64).sum().item())
+    Fk = int(nk.to(torch.int64).sum().item())
+
+    ms_per_step = elapsed_ms / args.steps
+    value = N * world / (ms_per_step * 1e-3) / 1e6
+    A = algorithmic_bytes(N, V, F, P, D, b)
+    peak, peak_kind = measured_hbm_peak()
+    dom = max(stage_ms, key=stage_ms.get)
+    kname = {"project": "k_project_count", "splat": "k_fill", "blend": "k_tile_blend",
+             "backward": "k_tile_backward"}[dom]
+    achieved = A[dom] / (stage_ms[dom] * 1e-3) / 1e9
+    step_bytes = sum(A.values())
+    roofline = {
+        "bound": "hbm", "kernel": kname, "stage": dom, "achieved": round(achieved, 1), "peak": peak,
+        "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+        "traffic": ncu_traffic(kname, args.workload),
+        "algorithmic_bytes": int(A[dom]),
+        "step": {"achieved": round(step_bytes / (ms_per_step * 1e-3) / 1e9, 1),
+                 "frac": round(step_bytes / (ms_per_step * 1e-3) / 1e9 / peak, 4),
+                 "algorithmic_bytes": int(step_bytes)},
+        "stages": {k: {"ms": round(v, 4), "algorithmic_bytes": int(A[k]),
+                       "frac": round(A[k] / (v * 1e-3) / 1e9 / peak, 4)} for k, v in stage_ms.items()},
+    }
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_pos = torch.from_numpy(sc.pos).pin_memory()
+        h_sw = torch.from_numpy(sc.size_w).pin_memory()
+        h_op = torch.from_numpy(sc.opacity).pin_memory()
+        h_desc = torch.from_numpy(sc.desc).to(desc_dtype).pin_memory()
+        h_out = [torch.empty(g.shape, dtype=torch.float32).pin_memory() for g in grads]
+        h2d = sum(t.numel() * t.element_size() for t in (h_pos, h_sw, h_op, h_desc))
+        d2h = sum(t.numel() * t.element_size() for t in h_out)
+
+        def e2e_step():
+            pos.copy_(h_pos, non_blocking=True)
+            sw.copy_(h_sw, non_blocking=True)
+            op.copy_(h_op, non_blocking=True)
+            desc.copy_(h_desc, non_blocking=True)
+            step()
+            for h, g in zip(h_out, grads):
+                h.copy_(g, non_blocking=True)
+
+        for _ in range(min(args.warmup, 3)):
+            e2e_step()
+        torch.cuda.synchronize(dev)
+        barrier(world, dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(world, dev)
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev) / args.steps
+        e2e = {"value": round(N * world / (e2e_ms * 1e-3) / 1e6, 3), "unit": "Mpoints/s",
+               "ms_per_step": round(e2e_ms, 4), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    # forward-only time (same frame, no backward), for the forward ms/frame figure
+    torch.cuda.synchronize(dev)
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.steps):
+        r.project(pos, sw, ws, records=rec)
+        r.splat_forward(rec, ws)
+        r.blend(rec, op, desc, ws, pyramid=pyr)
+    f1.record(stream)
+    torch.cuda.synchronize(dev)
+    fwd_ms = max_over_ranks(f0.elapsed_time(f1), world, dev) / args.steps
+    flags = r.status(ws)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(sc, args.cpu_frames)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 3), "unit": "Mpoints/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if b == 4 else "f32 (bf16 descriptors)",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "points": N, "width": sc.camera.width,
+                       "height": sc.camera.height, "layers": sc.n_layers, "K": sc.K, "D": D,
+                       "mode": args.mode, "tile": args.tile, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (216 MB of point inputs per step); no flush"},
+            "forward_ms": round(fwd_ms, 4), "fwd_bwd_ms": round(ms_per_step, 4),
+            "forward_mpoints_s": round(N / (fwd_ms * 1e-3) / 1e6, 3),
+            "counters": {"N": N, "V": V, "F": F, "Fk": Fk, "P": P},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": KERNELS_PER_STEP * args.steps, "clocks": clk, "device_flags": flags,
+        }
+        print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the CPU oracle (cpu_baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+
+def _oracle_frame_fwd_bwd(sc, G_seed=1):
+    import oracle
+
+    fr = oracle.Frame.from_scene(sc)
+    fr.render()
+    G = np.random.default_rng(G_seed).uniform(-1, 1, (fr.n_pix, sc.D))
+    fr.backward(G)
+
+
+def cpu_baseline(sc, frames):
+    import oracle
+
+    oracle.build()
+    t = time.perf_counter()
+    for _ in range(frames):
+        _oracle_frame_fwd_bwd(sc)
+    dt = (time.perf_counter() - t) / frames
+    return {"value": round(sc.n / dt / 1e6, 4), "unit": "Mpoints/s", "cores": 1, "kind": "oracle",
+            "sample": f"{frames} full frames of {sc.name}: fwd+bwd, float64 oracle, 1 thread",
+            "seconds_per_frame": round(dt, 3)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2401_06003_gb300 import scenes
+
+    oracle.build()
+    sc = scenes.make_config(args.workload)
+    rng = np.random.default_rng(7)
+    n_s = min(args.ref_sample, sc.n)
+    subs = [sc.subset(np.sort(rng.choice(sc.n, n_s, replace=False))) for _ in range(2)]
+    for w in range(args.warmup):
+        _oracle_frame_fwd_bwd(subs[w % 2])
+    times = []
+    for s in range(args.steps):
+        t = time.perf_counter()
+        _oracle_frame_fwd_bwd(subs[s % 2])
+        times.append(time.perf_counter() - t)
+    ms = 1e3 * float(np.mean(times))
+    value = n_s / (ms * 1e-3) / 1e6
+    sample = f"random {n_s}-point subset of {sc.name} per step (fwd+bwd, float64 oracle, 1 thread)"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "Mpoints/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "points": sc.n, "width": sc.camera.width,
+                   "height": sc.camera.height, "layers": sc.n_layers, "K": sc.K, "D": sc.D,
+                   "mode": "full lists (oracle)", "parallelism": "cpu"},
+        "cpu_baseline": {"value": round(value, 4), "unit": "Mpoints/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": "Mpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

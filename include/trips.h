@@ -1,0 +1,228 @@
+/*
+ * trips.h -- C ABI of the GB300 trilinear point splatting library (libtrips.so).
+ *
+ * The library renders a point cloud into a screen-space feature pyramid the
+ * way TRIPS does (Franke, Rueckert, Fink, Stamminger, "TRIPS: Trilinear Point
+ * Splatting for Real-Time Radiance Field Rendering", Eurographics 2024):
+ *
+ *   I = Phi(C, R, t, x, s_w, tau, alpha)                         (Sec. 3, Eq. 1)
+ *
+ * C are the camera intrinsics, (R, t) the pose, x the point positions, s_w
+ * the world-space point sizes, tau the point descriptors and alpha the point
+ * opacities.  The optional environment map E of Eq. 1 is not part of this
+ * library.  The frame is produced by four stream-ordered calls that follow the
+ * paper's three render stages (Sec. 3.6: collect, splat, sort-and-accumulate)
+ * and the backward pass:
+ *
+ *   tp_project        project, cull and choose layers (Sec. 3.1, Eq. 2)
+ *   tp_splat_forward  bin every (point, screen tile) pair of the trilinear
+ *                     2x2x2 splat into per-tile lists (Sec. 3.1, Eq. 3-5;
+ *                     Sec. 3.6 "counting", "offset scan", "splatting")
+ *   tp_blend          per pixel: the K front-most fragments by depth, blended
+ *                     front to back (Sec. 3.2, Eq. 6-7; Sec. 3.6)
+ *   tp_splat_backward gradients of a loss with respect to positions, world
+ *                     sizes, opacities and descriptors (Sec. 3.5, Sec. 3.6)
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Device pointers are CUDA device memory of the current device; host
+ *   pointers are marked "host".  The caller owns every buffer, including the
+ *   workspace.  The library never allocates or frees memory and never
+ *   synchronises the stream, except tp_get_status.
+ * - All work is enqueued on `stream` (NULL = the legacy default stream) in
+ *   call order.  The calls contain no host round trip, so a frame can be
+ *   captured in a CUDA graph.
+ * - One frame = one (tp_config, tp_camera, n, workspace) tuple; every call of
+ *   a frame must see the same values.
+ * - Argument errors are found on the host and returned before anything is
+ *   enqueued.  Errors found on the device are bits of a status word in the
+ *   workspace (TP_FLAG_*), read with tp_get_status.
+ * - A CUDA launch error is returned as TP_ERR_CUDA.
+ *
+ * Geometry (the readings of the paper this library implements)
+ * ------------------------------------------------------------
+ * - Pinhole camera, +z forward, +y down: X_c = R X_w + t,
+ *   x = fx X_c/Z_c + cx, y = fy Y_c/Z_c + cy, screen size s = fx s_w / Z_c
+ *   (Eq. 2), depth z = Z_c.  Points with Z_c <= znear are culled.
+ * - Pyramid layer L has W_L = ceil(W / 2^L) by H_L = ceil(H / 2^L) pixels.
+ *   Layer-L pixel (j, k) has its centre at ((j + 0.5) 2^L, (k + 0.5) 2^L).
+ * - s < 1: layer 0 only with iota = eps + (1 - eps) s (Eq. 5, second case).
+ *   1 <= s < 2^(n-1): layers floor(log2 s) and floor(log2 s) + 1 with the
+ *   linear weights of Eq. 5.  s >= 2^(n-1): layer n-1 only, iota = 1.
+ * - Fragments with an exactly zero bilinear or layer weight are not written;
+ *   taps outside a layer are dropped.
+ * - Per pixel, fragments are ordered by ascending (z, point index) and the
+ *   first K are kept (Sec. 3.2 and Sec. 3.6, K = 16 in the paper).
+ * - The projection and everything that decides an integer (culling, layer
+ *   pair, taps, order) is evaluated in IEEE float32 in this fixed order, with
+ *   no fused multiply-add: Xc = ((R0 X + R1 Y) + R2 Z) + t0 (likewise Yc, Zc),
+ *   x = (fx Xc)/Zc + cx, y = (fy Yc)/Zc + cy, s = (fx s_w)/Zc,
+ *   u = x 2^-L - 0.5, j0 = floor(u).
+ *
+ * Layouts
+ * -------
+ * - pos [n][3] float32, size_w [n], opacity [n] float32.
+ * - desc [n][D] float32 or bfloat16 (tp_config.desc_dtype), row-major.
+ * - point records [n][4] float32: (x, y, z, s) of each point, all zero for a
+ *   culled point.
+ * - pyramid [P][D] float32: layer L occupies rows
+ *   [layer_offsets[L], layer_offsets[L+1]), each layer row-major (row k,
+ *   column j).  P = tp_pyramid_pixels(...).
+ * - kept [P][K] uint32 point indices of the kept fragments in blend order,
+ *   0xFFFFFFFF past n_kept; n_kept [P] uint8; t_final [P] float32 is the
+ *   transmittance left after the kept fragments; n_frag [P] uint32 is the
+ *   number of candidate fragments of the pixel before the K cap.
+ *
+ * Sizes: n < 2^27 points, 1 <= n_layers <= 16, K in {4, 8, 16, 32},
+ * 1 <= D <= 64, width and height in [1, 32768].
+ */
+#ifndef TRIPS_H
+#define TRIPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TP_API __attribute__((visibility("default")))
+#else
+#define TP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st *tp_stream_t;
+
+typedef enum {
+    TP_OK = 0,
+    TP_ERR_INVALID_ARG = 1, /* null pointer, bad size or config (host check) */
+    TP_ERR_CAPACITY = 2,    /* workspace too small for the frame's tile lists */
+    TP_ERR_NONFINITE = 3,   /* a point had a non-finite input or s_w < 0; it was culled */
+    TP_ERR_TIMEOUT = 4,     /* a bounded device wait gave up */
+    TP_ERR_CUDA = 5,        /* a CUDA runtime call or launch failed */
+    TP_ERR_UNSUPPORTED = 6  /* valid but not supported by this build (e.g. K) */
+} tp_status;
+
+/* Bits of the device status word (tp_get_status). */
+#define TP_FLAG_NONFINITE 0x1u
+#define TP_FLAG_CAPACITY 0x2u
+#define TP_FLAG_TIMEOUT 0x4u
+
+/* Pinhole camera; R is row-major world->camera, X_c = R X_w + t. */
+typedef struct {
+    float fx, fy, cx, cy;
+    float R[9];
+    float t[3];
+    float znear;
+    int32_t width, height;
+} tp_camera;
+
+enum { TP_F32 = 0, TP_BF16 = 1 };
+enum { TP_STORE_LISTS = 0, TP_RECOMPUTE = 1 };
+
+typedef struct {
+    int32_t n_layers;   /* pyramid layers n (the paper uses 4-8, Tab. "layers_num") */
+    int32_t K;          /* per-pixel list cap (16 in the paper, Sec. 3.2) */
+    int32_t desc_dim;   /* descriptor width D (4 in the paper, Tab. "feature_num") */
+    float eps;          /* minimum sub-pixel layer weight (0.25, Eq. 5) */
+    int32_t desc_dtype; /* TP_F32 or TP_BF16 */
+    int32_t mode;       /* TP_STORE_LISTS or TP_RECOMPUTE (see tp_splat_backward) */
+    int32_t tile_w;     /* screen tile of the binning and blend kernels, in pixels */
+    int32_t tile_h;     /*   of each layer; 0 = the default 16 x 16 */
+} tp_config;
+
+/*
+ * Number of pyramid pixels P = sum_L W_L H_L.  If layer_offsets is not NULL
+ * (host, [n_layers + 1]) it receives the first pyramid row of each layer and
+ * P at the end.  Returns -1 on bad arguments.
+ */
+TP_API int64_t tp_pyramid_pixels(const tp_camera *cam, int32_t n_layers, int64_t *layer_offsets);
+
+/*
+ * Bytes of workspace a frame needs.  entry_capacity is the number of
+ * (point, tile) pairs the tile lists can hold; <= 0 selects 8 n, which can
+ * never overflow (a point touches at most 2 x 2 tiles in each of its two
+ * layers).  Returns -1 on bad arguments.  The workspace must be 256-byte
+ * aligned.
+ */
+TP_API int64_t tp_workspace_bytes(const tp_config *cfg, const tp_camera *cam, int64_t n_points, int64_t entry_capacity);
+
+/*
+ * Collect stage (Sec. 3.1 Eq. 2, Sec. 3.6 first stage): project each point,
+ * cull it (Z_c <= znear, non-finite input, s_w < 0), compute its screen size
+ * and layer pair, and count the (point, tile) pairs of every screen tile.
+ *   pos [n][3], size_w [n] (device, read)
+ *   records [n][4] (device, written): (x, y, z, s), zeros when culled
+ *   ws, ws_bytes: workspace (device); this call resets its status word.
+ * Non-finite inputs set TP_FLAG_NONFINITE; the point is culled and the frame
+ * still renders.
+ */
+TP_API tp_status tp_project(const tp_config *cfg, const tp_camera *cam, int64_t n, const float *pos, const float *size_w,
+                     float *records, void *ws, int64_t ws_bytes, tp_stream_t stream);
+
+/*
+ * Offset scan and splatting stages (Sec. 3.6): exclusive scan of the tile
+ * counts, then every point writes its record and index into the list of
+ * each screen tile its 2x2x2 splat touches.  Needs tp_project of the same
+ * frame first.  If the lists exceed the workspace's entry capacity,
+ * TP_FLAG_CAPACITY is set and the frame's outputs are not valid.
+ */
+TP_API tp_status tp_splat_forward(const tp_config *cfg, const tp_camera *cam, int64_t n, const float *records, void *ws,
+                           int64_t ws_bytes, tp_stream_t stream);
+
+/*
+ * Sort-and-accumulate stage (Sec. 3.2 Eq. 6-7, Sec. 3.6): for every pyramid
+ * pixel, the K smallest (z, index) fragments in order, blended front to back:
+ *   C = sum_m T_m gamma_m tau_m,  T_m = prod_{i<m} (1 - gamma_i),
+ *   gamma = beta iota alpha (Eq. 3).
+ *   records [n][4], opacity [n], desc [n][D] (device, read)
+ *   pyramid [P][D] (device, written; every pixel)
+ *   kept [P][K], n_kept [P], t_final [P], n_frag [P] (device, written;
+ *   each may be NULL).  kept and n_kept are what tp_splat_backward reads in
+ *   TP_STORE_LISTS mode.
+ */
+TP_API tp_status tp_blend(const tp_config *cfg, const tp_camera *cam, int64_t n, const float *records, const float *opacity,
+                   const void *desc, float *pyramid, uint32_t *kept, uint8_t *n_kept, float *t_final,
+                   uint32_t *n_frag, void *ws, int64_t ws_bytes, tp_stream_t stream);
+
+/*
+ * Backward pass (Sec. 3.6 "for the backwards pass, the sorted per-pixel lists
+ * are stored"; the paper optimises positions, sizes and descriptors,
+ * Sec. 3.5).  Given G = dL/dpyramid [P][D] (device), writes
+ *   grad_pos [n][3], grad_size_w [n], grad_opacity [n], grad_desc [n][D]
+ * (device float32, overwritten; every entry, zero where a point has no kept
+ * fragment).  With kept and n_kept (TP_STORE_LISTS) the per-pixel lists come
+ * from tp_blend.  With kept == NULL (TP_RECOMPUTE) the lists are rebuilt from
+ * the workspace's tile lists, which must still hold this frame's
+ * tp_splat_forward result.  The adjoint of one pixel runs back to front:
+ *   R_M = 0,  dL/dgamma_m = T_m (G.tau_m - R_m),
+ *   R_{m-1} = gamma_m G.tau_m + (1 - gamma_m) R_m,  dL/dtau_m = T_m gamma_m G,
+ * and chains through gamma = beta iota alpha to alpha, the screen position
+ * (x, y), the screen size s, and from there to X_w and s_w.
+ */
+TP_API tp_status tp_splat_backward(const tp_config *cfg, const tp_camera *cam, int64_t n, const float *records,
+                            const float *opacity, const void *desc, const uint32_t *kept, const uint8_t *n_kept,
+                            const float *grad_pyramid, float *grad_pos, float *grad_size_w, float *grad_opacity,
+                            float *grad_desc, void *ws, int64_t ws_bytes, tp_stream_t stream);
+
+/*
+ * Synchronises `stream` and reads the workspace's device status word into
+ * *device_flags (host; TP_FLAG_* bits).  Returns TP_ERR_CAPACITY,
+ * TP_ERR_TIMEOUT or TP_ERR_NONFINITE for the first set bit in that order,
+ * TP_OK if none is set.
+ */
+TP_API tp_status tp_get_status(const void *ws, tp_stream_t stream, int32_t *device_flags);
+
+/* Static string for a status code. */
+TP_API const char *tp_status_string(tp_status status);
+
+/* Library version, 100 * major + minor. */
+TP_API int32_t tp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TRIPS_H */

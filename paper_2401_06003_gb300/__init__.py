@@ -1,0 +1,11 @@
+"""GB300-native differentiable trilinear point splatting (the TRIPS render path).
+
+The compute lives in ``libtrips.so`` (CUDA for sm_103a, C ABI in
+``include/trips.h``); this package builds it in-tree, binds it with ctypes
+and exposes a ``torch.autograd.Function`` over it.
+"""
+from . import scenes  # noqa: F401
+from ._lib import TripsError, load  # noqa: F401
+from .splat import Frame, Renderer, TripsSplat, splat  # noqa: F401
+
+__all__ = ["Renderer", "TripsSplat", "splat", "Frame", "TripsError", "load", "scenes"]

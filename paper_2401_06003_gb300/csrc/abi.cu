@@ -1,0 +1,261 @@
+// abi.cu -- the extern "C" entry points declared in include/trips.h.
+//
+// Host-side argument checks, the frame description (pyramid layout and
+// screen-tile table), the workspace layout, and the kernel launches.  No
+// call allocates, frees or synchronises, except tp_get_status.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace {
+
+using tpk::Frame;
+using tpk::Workspace;
+
+constexpr int64_t kAlign = 256;
+constexpr int64_t kMaxPoints = (int64_t)1 << 27;
+constexpr size_t kMaxTileSmem = 200 * 1024;
+
+int64_t align_up(int64_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+bool valid_camera(const tp_camera *cam)
+{
+    if (!cam) return false;
+    if (cam->width < 1 || cam->height < 1 || cam->width > 32768 || cam->height > 32768) return false;
+    const float *f = &cam->fx;
+    for (int q = 0; q < 17; ++q)
+        if (!std::isfinite(f[q])) return false;
+    if (!(cam->znear > 0.0f)) return false;
+    if (cam->fx == 0.0f || cam->fy == 0.0f) return false;
+    return true;
+}
+
+void fill_layers(const tp_camera *cam, int n_layers, Frame &F)
+{
+    F.pix_base[0] = 0;
+    for (int L = 0; L < n_layers; ++L) {
+        const int64_t s = (int64_t)1 << L;
+        F.lw[L] = (int)((cam->width + s - 1) / s);
+        F.lh[L] = (int)((cam->height + s - 1) / s);
+        F.pix_base[L + 1] = F.pix_base[L] + (long long)F.lw[L] * F.lh[L];
+    }
+}
+
+// Builds the frame description; TP_OK or the reason it is invalid.
+tp_status make_frame(const tp_config *cfg, const tp_camera *cam, Frame &F)
+{
+    if (!cfg || !valid_camera(cam)) return TP_ERR_INVALID_ARG;
+    if (cfg->n_layers < 1 || cfg->n_layers > tpk::kMaxLayers) return TP_ERR_INVALID_ARG;
+    if (cfg->desc_dim < 1 || cfg->desc_dim > 64) return TP_ERR_INVALID_ARG;
+    if (!(cfg->eps >= 0.0f && cfg->eps <= 1.0f)) return TP_ERR_INVALID_ARG;
+    if (cfg->desc_dtype != TP_F32 && cfg->desc_dtype != TP_BF16) return TP_ERR_INVALID_ARG;
+    if (cfg->mode != TP_STORE_LISTS && cfg->mode != TP_RECOMPUTE) return TP_ERR_INVALID_ARG;
+    if (cfg->K < 1 || cfg->K > 255) return TP_ERR_INVALID_ARG;
+    if (cfg->K != 4 && cfg->K != 8 && cfg->K != 16 && cfg->K != 32) return TP_ERR_UNSUPPORTED;
+    const int tw = cfg->tile_w > 0 ? cfg->tile_w : 16;
+    const int th = cfg->tile_h > 0 ? cfg->tile_h : 16;
+    if (tw > 64 || th > 64 || cfg->tile_w < 0 || cfg->tile_h < 0) return TP_ERR_INVALID_ARG;
+    const size_t smem = (size_t)tw * th * ((size_t)cfg->K * 8 + 4);
+    if (smem > kMaxTileSmem) return TP_ERR_UNSUPPORTED;
+    std::memset(&F, 0, sizeof(F));
+    F.fx = cam->fx; F.fy = cam->fy; F.cx = cam->cx; F.cy = cam->cy;
+    std::memcpy(F.R, cam->R, sizeof(F.R));
+    std::memcpy(F.t, cam->t, sizeof(F.t));
+    F.znear = cam->znear;
+    F.eps = cfg->eps;
+    F.n_layers = cfg->n_layers;
+    F.K = cfg->K;
+    F.D = cfg->desc_dim;
+    F.tile_w = tw;
+    F.tile_h = th;
+    fill_layers(cam, cfg->n_layers, F);
+    int tiles = 0;
+    for (int L = 0; L < F.n_layers; ++L) {
+        F.tile_base[L] = tiles;
+        F.tiles_x[L] = (F.lw[L] + tw - 1) / tw;
+        F.tiles_y[L] = (F.lh[L] + th - 1) / th;
+        const int64_t t = (int64_t)tiles + (int64_t)F.tiles_x[L] * F.tiles_y[L];
+        if (t > (1 << 30)) return TP_ERR_INVALID_ARG;
+        tiles = (int)t;
+    }
+    F.tile_base[F.n_layers] = tiles;
+    F.n_tiles = tiles;
+    return TP_OK;
+}
+
+struct WsLayout {
+    int64_t count, off, cursor, idx, rec, end;
+};
+
+WsLayout layout_for(const Frame &F, int64_t capacity)
+{
+    WsLayout w;
+    const int64_t T = F.n_tiles;
+    w.count = kAlign;
+    w.off = align_up(w.count + 4 * T);
+    w.cursor = align_up(w.off + 4 * (T + 1));
+    w.idx = align_up(w.cursor + 4 * T);
+    w.rec = align_up(w.idx + 4 * capacity);
+    w.end = w.rec + 16 * capacity;
+    return w;
+}
+
+// Entry capacity that fits in ws_bytes (largest c with layout_for(c).end <= ws_bytes).
+int64_t capacity_for(const Frame &F, int64_t ws_bytes)
+{
+    const WsLayout w0 = layout_for(F, 0);
+    if (ws_bytes < w0.end) return -1;
+    int64_t c = (ws_bytes - w0.end - 2 * kAlign) / 20;
+    if (c < 0) c = 0;
+    while (c > 0 && layout_for(F, c).end > ws_bytes) --c;
+    if (c > 0x7FFFFFFF) c = 0x7FFFFFFF;
+    return c;
+}
+
+tp_status bind_workspace(const Frame &F, void *ws, int64_t ws_bytes, Workspace &W)
+{
+    if (!ws || ((uintptr_t)ws % kAlign) != 0) return TP_ERR_INVALID_ARG;
+    const int64_t cap = capacity_for(F, ws_bytes);
+    if (cap < 0) return TP_ERR_INVALID_ARG;
+    const WsLayout w = layout_for(F, cap);
+    char *base = static_cast<char *>(ws);
+    W.status = reinterpret_cast<unsigned *>(base);
+    W.tile_count = reinterpret_cast<unsigned *>(base + w.count);
+    W.tile_off = reinterpret_cast<unsigned *>(base + w.off);
+    W.tile_cursor = reinterpret_cast<unsigned *>(base + w.cursor);
+    W.bucket_idx = reinterpret_cast<unsigned *>(base + w.idx);
+    W.bucket_rec = reinterpret_cast<float4 *>(base + w.rec);
+    W.capacity = (unsigned)cap;
+    return TP_OK;
+}
+
+tp_status common_checks(const tp_config *cfg, const tp_camera *cam, int64_t n, void *ws, int64_t ws_bytes,
+                        Frame &F, Workspace &W)
+{
+    if (n < 0 || n >= kMaxPoints) return TP_ERR_INVALID_ARG;
+    tp_status s = make_frame(cfg, cam, F);
+    if (s != TP_OK) return s;
+    return bind_workspace(F, ws, ws_bytes, W);
+}
+
+tp_status from_cuda(cudaError_t e) { return e == cudaSuccess ? TP_OK : TP_ERR_CUDA; }
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+}  // namespace
+
+extern "C" {
+
+int64_t tp_pyramid_pixels(const tp_camera *cam, int32_t n_layers, int64_t *layer_offsets)
+{
+    if (!valid_camera(cam) || n_layers < 1 || n_layers > tpk::kMaxLayers) return -1;
+    Frame F;
+    std::memset(&F, 0, sizeof(F));
+    fill_layers(cam, n_layers, F);
+    if (layer_offsets)
+        for (int L = 0; L <= n_layers; ++L) layer_offsets[L] = F.pix_base[L];
+    return F.pix_base[n_layers];
+}
+
+int64_t tp_workspace_bytes(const tp_config *cfg, const tp_camera *cam, int64_t n_points, int64_t entry_capacity)
+{
+    Frame F;
+    if (n_points < 0 || n_points >= kMaxPoints) return -1;
+    if (make_frame(cfg, cam, F) != TP_OK) return -1;
+    int64_t cap = entry_capacity > 0 ? entry_capacity : 8 * n_points;
+    if (cap < 1) cap = 1;
+    if (cap > 0x7FFFFFFF) cap = 0x7FFFFFFF;
+    return layout_for(F, cap).end;
+}
+
+tp_status tp_project(const tp_config *cfg, const tp_camera *cam, int64_t n, const float *pos, const float *size_w,
+                     float *records, void *ws, int64_t ws_bytes, tp_stream_t stream)
+{
+    Frame F;
+    Workspace W;
+    tp_status s = common_checks(cfg, cam, n, ws, ws_bytes, F, W);
+    if (s != TP_OK) return s;
+    if (n > 0 && (!pos || !size_w || !records || !aligned16(records))) return TP_ERR_INVALID_ARG;
+    return from_cuda(tpk::launch_project_count(F, W, n, pos, size_w, reinterpret_cast<float4 *>(records),
+                                               (cudaStream_t)stream));
+}
+
+tp_status tp_splat_forward(const tp_config *cfg, const tp_camera *cam, int64_t n, const float *records, void *ws,
+                           int64_t ws_bytes, tp_stream_t stream)
+{
+    Frame F;
+    Workspace W;
+    tp_status s = common_checks(cfg, cam, n, ws, ws_bytes, F, W);
+    if (s != TP_OK) return s;
+    if (n > 0 && (!records || !aligned16(records))) return TP_ERR_INVALID_ARG;
+    return from_cuda(
+        tpk::launch_scan_fill(F, W, n, reinterpret_cast<const float4 *>(records), (cudaStream_t)stream));
+}
+
+tp_status tp_blend(const tp_config *cfg, const tp_camera *cam, int64_t n, const float *records, const float *opacity,
+                   const void *desc, float *pyramid, uint32_t *kept, uint8_t *n_kept, float *t_final,
+                   uint32_t *n_frag, void *ws, int64_t ws_bytes, tp_stream_t stream)
+{
+    Frame F;
+    Workspace W;
+    tp_status s = common_checks(cfg, cam, n, ws, ws_bytes, F, W);
+    if (s != TP_OK) return s;
+    if (!pyramid) return TP_ERR_INVALID_ARG;
+    if (n > 0 && (!records || !opacity || !desc || !aligned16(records))) return TP_ERR_INVALID_ARG;
+    return from_cuda(tpk::launch_blend(F, W, reinterpret_cast<const float4 *>(records), opacity, desc,
+                                       cfg->desc_dtype, pyramid, kept, n_kept, t_final, n_frag,
+                                       (cudaStream_t)stream));
+}
+
+tp_status tp_splat_backward(const tp_config *cfg, const tp_camera *cam, int64_t n, const float *records,
+                            const float *opacity, const void *desc, const uint32_t *kept, const uint8_t *n_kept,
+                            const float *grad_pyramid, float *grad_pos, float *grad_size_w, float *grad_opacity,
+                            float *grad_desc, void *ws, int64_t ws_bytes, tp_stream_t stream)
+{
+    Frame F;
+    Workspace W;
+    tp_status s = common_checks(cfg, cam, n, ws, ws_bytes, F, W);
+    if (s != TP_OK) return s;
+    if ((kept == nullptr) != (n_kept == nullptr)) return TP_ERR_INVALID_ARG;
+    if (!grad_pyramid) return TP_ERR_INVALID_ARG;
+    if (n > 0 && (!records || !opacity || !desc || !grad_pos || !grad_size_w || !grad_opacity || !grad_desc ||
+                  !aligned16(records)))
+        return TP_ERR_INVALID_ARG;
+    return from_cuda(tpk::launch_backward(F, W, n, reinterpret_cast<const float4 *>(records), opacity, desc,
+                                          cfg->desc_dtype, kept, n_kept, grad_pyramid, grad_pos, grad_size_w,
+                                          grad_opacity, grad_desc, (cudaStream_t)stream));
+}
+
+tp_status tp_get_status(const void *ws, tp_stream_t stream, int32_t *device_flags)
+{
+    if (!ws || !device_flags) return TP_ERR_INVALID_ARG;
+    unsigned flags = 0;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&flags, ws, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return TP_ERR_CUDA;
+    *device_flags = (int32_t)flags;
+    if (flags & TP_FLAG_CAPACITY) return TP_ERR_CAPACITY;
+    if (flags & TP_FLAG_TIMEOUT) return TP_ERR_TIMEOUT;
+    if (flags & TP_FLAG_NONFINITE) return TP_ERR_NONFINITE;
+    return TP_OK;
+}
+
+const char *tp_status_string(tp_status status)
+{
+    switch (status) {
+    case TP_OK: return "ok";
+    case TP_ERR_INVALID_ARG: return "invalid argument";
+    case TP_ERR_CAPACITY: return "workspace entry capacity exceeded";
+    case TP_ERR_NONFINITE: return "non-finite point input (point culled)";
+    case TP_ERR_TIMEOUT: return "bounded device wait timed out";
+    case TP_ERR_CUDA: return "CUDA error";
+    case TP_ERR_UNSUPPORTED: return "unsupported configuration";
+    }
+    return "unknown status";
+}
+
+int32_t tp_version(void) { return 100; }
+
+}  // extern "C"

@@ -1,0 +1,148 @@
+// bin.cu -- collect, offset-scan and splat stages (TRIPS Sec. 3.6).
+//
+// The paper's collect pass projects every point and counts the elements of
+// every pixel list; an offset scan turns the counts into positions in one
+// continuous array; the splatting pass then writes (z, i) pairs into those
+// lists.  Here the lists are per screen tile instead of per pixel: a point's
+// 2x2x2 splat touches at most 2x2 tiles in each of its two layers, so the
+// count and fill passes make 1-2 global atomics per point instead of 4-8,
+// and the per-pixel lists are formed later in shared memory by the blend
+// kernel (blend.cu), which reads each tile's points with coalesced loads.
+#include "common.cuh"
+
+namespace tpk {
+
+// Calls fn(tile) for every screen tile the point's taps touch, at each of
+// its layers.  The taps and layers are exactly those of the blend kernels.
+template <class Fn>
+__device__ __forceinline__ void for_each_tile(const Frame &F, const float4 &r, Fn &&fn)
+{
+    const LayerPair lp = layer_pair(r.w, F.n_layers, F.eps);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        if (q >= lp.n) break;
+        const int L = lp.L[q];
+        const AxisTaps tx = axis_taps(r.x, L, F.lw[L]);
+        const AxisTaps ty = axis_taps(r.y, L, F.lh[L]);
+        int x0, x1, y0, y1;
+        if (!tap_tile_range(tx, F.tile_w, x0, x1) || !tap_tile_range(ty, F.tile_h, y0, y1)) continue;
+        const int base = F.tile_base[L];
+        const int tpr = F.tiles_x[L];
+        for (int b = y0; b <= y1; ++b)
+            for (int a = x0; a <= x1; ++a) fn(base + b * tpr + a);
+    }
+}
+
+// Collect: project, cull, write the record and count (point, tile) pairs.
+__global__ void __launch_bounds__(kBlock) k_project_count(Frame F, Workspace W, long long n,
+                                                          const float *__restrict__ pos,
+                                                          const float *__restrict__ size_w, float4 *__restrict__ rec)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float X = __ldg(pos + 3 * i), Y = __ldg(pos + 3 * i + 1), Z = __ldg(pos + 3 * i + 2);
+        float4 r;
+        bool bad;
+        const bool vis = project_point(F, X, Y, Z, __ldg(size_w + i), r, bad);
+        if (bad) raise_flag(W.status, TP_FLAG_NONFINITE);
+        if (!vis) {
+            rec[i] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            continue;
+        }
+        rec[i] = r;
+        for_each_tile(F, r, [&](int t) { atomicAdd(W.tile_count + t, 1u); });
+    }
+}
+
+// Offset scan of the tile counts (one CTA; the tile count is small).
+__global__ void __launch_bounds__(1024) k_scan_tiles(Frame F, Workspace W)
+{
+    __shared__ unsigned warp_tot[32];
+    const int T = F.n_tiles;
+    const int per = (T + blockDim.x - 1) / blockDim.x;
+    const int beg = min(T, (int)threadIdx.x * per);
+    const int end = min(T, beg + per);
+    unsigned sum = 0;
+    for (int q = beg; q < end; ++q) sum += W.tile_count[q];
+    // inclusive warp scan
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned v = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    if (lane == 31) warp_tot[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned w = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        warp_tot[lane] = w;  // inclusive over warps
+    }
+    __syncthreads();
+    unsigned run = v - sum + (warp > 0 ? warp_tot[warp - 1] : 0u);
+    for (int q = beg; q < end; ++q) {
+        const unsigned c = W.tile_count[q];
+        W.tile_off[q] = run;
+        W.tile_cursor[q] = 0u;
+        run += c;
+    }
+    if (threadIdx.x == 0) {
+        const unsigned total = warp_tot[(blockDim.x >> 5) - 1];
+        W.tile_off[T] = total;
+        if (total > W.capacity) raise_flag(W.status, TP_FLAG_CAPACITY);
+    }
+}
+
+// Splat: every point appends its record and index to each tile it touches.
+__global__ void __launch_bounds__(kBlock) k_fill(Frame F, Workspace W, long long n, const float4 *__restrict__ rec)
+{
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float4 r = rec[i];
+        if (!(r.z > 0.0f)) continue;  // culled
+        for_each_tile(F, r, [&](int t) {
+            const unsigned e = W.tile_off[t] + atomicAdd(W.tile_cursor + t, 1u);
+            if (e < W.capacity) {
+                W.bucket_rec[e] = r;
+                W.bucket_idx[e] = (unsigned)i;
+            }
+        });
+    }
+}
+
+static int grid_for(long long n)
+{
+    long long b = (n + kBlock - 1) / kBlock;
+    if (b < 1) b = 1;
+    if (b > 152 * 32) b = 152 * 32;
+    return (int)b;
+}
+
+cudaError_t launch_project_count(const Frame &F, const Workspace &W, long long n, const float *pos,
+                                 const float *size_w, float4 *rec, cudaStream_t stream)
+{
+    cudaError_t e = cudaMemsetAsync(W.status, 0, sizeof(unsigned), stream);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(W.tile_count, 0, sizeof(unsigned) * (size_t)F.n_tiles, stream);
+    if (e != cudaSuccess) return e;
+    if (n == 0) return cudaSuccess;
+    k_project_count<<<grid_for(n), kBlock, 0, stream>>>(F, W, n, pos, size_w, rec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_fill(const Frame &F, const Workspace &W, long long n, const float4 *rec,
+                             cudaStream_t stream)
+{
+    k_scan_tiles<<<1, 1024, 0, stream>>>(F, W);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || n == 0) return e;
+    k_fill<<<grid_for(n), kBlock, 0, stream>>>(F, W, n, rec);
+    return cudaGetLastError();
+}
+
+}  // namespace tpk

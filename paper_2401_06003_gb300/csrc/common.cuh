@@ -1,0 +1,243 @@
+// common.cuh -- device-side data and arithmetic shared by the splatting kernels.
+//
+// The arithmetic here is the float32 evaluation of TRIPS' trilinear point
+// splat (Franke et al. 2024): projection and screen size (Sec. 3.1, Eq. 2),
+// layer pair and layer weight iota (Sec. 3.1, Eq. 5), bilinear taps beta
+// (Eq. 4).  Every operation that decides an integer (culling, layers, taps,
+// depth order) is written with explicit round-to-nearest intrinsics so the
+// compiler cannot fuse or reorder it; the order is the one documented in
+// include/trips.h.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "trips.h"
+
+namespace tpk {
+
+constexpr int kMaxLayers = 16;
+constexpr int kBlock = 256;  // threads per CTA of every kernel
+constexpr unsigned long long kEmptyKey = ~0ull;
+constexpr unsigned kNoPoint = 0xFFFFFFFFu;
+
+// Everything a kernel needs to know about one frame (passed by value).
+struct Frame {
+    float fx, fy, cx, cy;
+    float R[9];
+    float t[3];
+    float znear, eps;
+    int n_layers, K, D;
+    int tile_w, tile_h;
+    int n_tiles;
+    int lw[kMaxLayers], lh[kMaxLayers];            // layer sizes W_L, H_L
+    int tiles_x[kMaxLayers], tiles_y[kMaxLayers];  // tiles per layer row / column
+    int tile_base[kMaxLayers + 1];                 // first tile id of each layer
+    long long pix_base[kMaxLayers + 1];            // first pyramid pixel of each layer
+};
+
+// Device pointers into the caller's workspace.
+struct Workspace {
+    unsigned *status;       // [1] TP_FLAG_* bits
+    unsigned *tile_count;   // [n_tiles] (point, tile) pairs per tile
+    unsigned *tile_off;     // [n_tiles + 1] exclusive scan of tile_count
+    unsigned *tile_cursor;  // [n_tiles] fill cursors
+    unsigned *bucket_idx;   // [capacity] point index of each (point, tile) entry
+    float4 *bucket_rec;     // [capacity] point record of each entry
+    unsigned capacity;
+};
+
+// ---------------------------------------------------------------------------
+// Projection (Eq. 2), float32 in the documented order, no contraction.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool project_point(const Frame &F, float X, float Y, float Z, float sw, float4 &rec,
+                                              bool &bad)
+{
+    bad = false;
+    if (!(isfinite(X) && isfinite(Y) && isfinite(Z) && isfinite(sw)) || sw < 0.0f) {
+        bad = true;
+        return false;
+    }
+    float xc = __fmul_rn(F.R[0], X);
+    xc = __fadd_rn(xc, __fmul_rn(F.R[1], Y));
+    xc = __fadd_rn(xc, __fmul_rn(F.R[2], Z));
+    xc = __fadd_rn(xc, F.t[0]);
+    float yc = __fmul_rn(F.R[3], X);
+    yc = __fadd_rn(yc, __fmul_rn(F.R[4], Y));
+    yc = __fadd_rn(yc, __fmul_rn(F.R[5], Z));
+    yc = __fadd_rn(yc, F.t[1]);
+    float zc = __fmul_rn(F.R[6], X);
+    zc = __fadd_rn(zc, __fmul_rn(F.R[7], Y));
+    zc = __fadd_rn(zc, __fmul_rn(F.R[8], Z));
+    zc = __fadd_rn(zc, F.t[2]);
+    if (!(zc > F.znear)) return false;
+    float x = __fadd_rn(__fdiv_rn(__fmul_rn(F.fx, xc), zc), F.cx);
+    float y = __fadd_rn(__fdiv_rn(__fmul_rn(F.fy, yc), zc), F.cy);
+    float s = __fdiv_rn(__fmul_rn(F.fx, sw), zc);
+    if (!(isfinite(x) && isfinite(y) && isfinite(s))) {
+        bad = true;
+        return false;
+    }
+    rec = make_float4(x, y, zc, s);
+    return true;
+}
+
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }  // exact 2^e
+
+// ---------------------------------------------------------------------------
+// Layer pair and layer weights iota (Sec. 3.1, Eq. 5).
+// ---------------------------------------------------------------------------
+struct LayerPair {
+    int n;            // 1 or 2 layers
+    int L[2];
+    float iota[2];
+    float diota[2];   // d iota / d s
+};
+
+__device__ __forceinline__ LayerPair layer_pair(float s, int n_layers, float eps)
+{
+    LayerPair p;
+    if (s < 1.0f) {  // sub-pixel point: finest layer, iota >= eps
+        p.n = 1;
+        p.L[0] = 0;
+        p.iota[0] = __fadd_rn(eps, __fmul_rn(__fsub_rn(1.0f, eps), s));
+        p.diota[0] = __fsub_rn(1.0f, eps);
+        return p;
+    }
+    const unsigned b = __float_as_uint(s);
+    const int Ll = int(b >> 23) - 127;  // floor(log2 s), exact for normal s >= 1
+    if (Ll >= n_layers - 1) {           // beyond the coarsest layer: clamp
+        p.n = 1;
+        p.L[0] = n_layers - 1;
+        p.iota[0] = 1.0f;
+        p.diota[0] = 0.0f;
+        return p;
+    }
+    const float pl = pow2f(Ll), inv = pow2f(-Ll);
+    p.L[0] = Ll;
+    p.iota[0] = __fmul_rn(__fsub_rn(__fmul_rn(2.0f, pl), s), inv);  // (2^Lu - s) / 2^Ll, exact
+    p.diota[0] = -inv;
+    if ((b & 0x7FFFFFu) == 0u) {  // s = 2^Ll: the upper weight is exactly zero
+        p.n = 1;
+    } else {
+        p.n = 2;
+        p.L[1] = Ll + 1;
+        p.iota[1] = __fmul_rn(__fsub_rn(s, pl), inv);  // (s - 2^Ll) / 2^Ll, exact
+        p.diota[1] = inv;
+    }
+    return p;
+}
+
+// iota of layer L for a point of screen size s; false if the point is not in layer L.
+__device__ __forceinline__ bool layer_weight(float s, int L, int n_layers, float eps, float &iota, float &diota)
+{
+    LayerPair p = layer_pair(s, n_layers, eps);
+    if (p.L[0] == L) {
+        iota = p.iota[0];
+        diota = p.diota[0];
+        return true;
+    }
+    if (p.n == 2 && p.L[1] == L) {
+        iota = p.iota[1];
+        diota = p.diota[1];
+        return true;
+    }
+    return false;
+}
+
+// ---------------------------------------------------------------------------
+// Bilinear taps along one axis at layer L (Eq. 4): pixel centres at j + 0.5.
+// ---------------------------------------------------------------------------
+struct AxisTaps {
+    int j0;     // first tap index floor(u)
+    float a;    // u - j0: weight of tap j0 + 1; tap j0 has 1 - a
+    bool t0;    // tap j0 exists and is inside the layer
+    bool t1;    // tap j0 + 1 exists (a != 0) and is inside the layer
+};
+
+__device__ __forceinline__ AxisTaps axis_taps(float pos, int L, int extent)
+{
+    AxisTaps t;
+    t.j0 = 0;
+    t.a = 0.0f;
+    t.t0 = t.t1 = false;
+    const float u = __fsub_rn(__fmul_rn(pos, pow2f(-L)), 0.5f);
+    if (!(u > -2.0f && u < __int2float_rn(extent) + 1.0f)) return t;
+    const float fl = floorf(u);
+    t.j0 = __float2int_rz(fl);
+    t.a = __fsub_rn(u, fl);
+    t.t0 = t.j0 >= 0 && t.j0 < extent;
+    t.t1 = t.a != 0.0f && t.j0 + 1 >= 0 && t.j0 + 1 < extent;
+    return t;
+}
+
+// Weight and derivative (w.r.t. the full-resolution coordinate) of tap j.
+__device__ __forceinline__ void tap_weight(const AxisTaps &t, int j, int L, float &w, float &dw)
+{
+    const float scale = pow2f(-L);
+    if (j == t.j0) {
+        w = __fsub_rn(1.0f, t.a);
+        dw = -scale;
+    } else {
+        w = t.a;
+        dw = scale;
+    }
+}
+
+// Inclusive range of tiles along one axis touched by the taps; false if none.
+__device__ __forceinline__ bool tap_tile_range(const AxisTaps &t, int tile, int &lo, int &hi)
+{
+    if (!t.t0 && !t.t1) return false;
+    const int jmin = t.t0 ? t.j0 : t.j0 + 1;
+    const int jmax = t.t1 ? t.j0 + 1 : t.j0;
+    lo = jmin / tile;
+    hi = jmax / tile;
+    return true;
+}
+
+// Sort key of a fragment: depth bits (z > 0, so the bits order like the
+// values) above the point index, which breaks ties.
+__device__ __forceinline__ unsigned long long frag_key(float z, unsigned i)
+{
+    return ((unsigned long long)__float_as_uint(z) << 32) | (unsigned long long)i;
+}
+
+__device__ __forceinline__ int tile_layer(const Frame &F, int tile)
+{
+    int L = 0;
+    while (L + 1 < F.n_layers && tile >= F.tile_base[L + 1]) ++L;
+    return L;
+}
+
+__device__ __forceinline__ void raise_flag(unsigned *status, unsigned bit)
+{
+    if ((*((volatile unsigned *)status) & bit) == 0u) atomicOr(status, bit);
+}
+
+template <typename T>
+__device__ __forceinline__ float load_desc(const T *p);
+template <>
+__device__ __forceinline__ float load_desc<float>(const float *p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ float load_desc<__nv_bfloat16>(const __nv_bfloat16 *p)
+{
+    return __bfloat162float(*p);
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (defined in bin.cu and blend.cu).
+// ---------------------------------------------------------------------------
+cudaError_t launch_project_count(const Frame &F, const Workspace &W, long long n, const float *pos,
+                                 const float *size_w, float4 *rec, cudaStream_t stream);
+cudaError_t launch_scan_fill(const Frame &F, const Workspace &W, long long n, const float4 *rec,
+                             cudaStream_t stream);
+cudaError_t launch_blend(const Frame &F, const Workspace &W, const float4 *rec, const float *opacity,
+                         const void *desc, int desc_dtype, float *pyramid, unsigned *kept, unsigned char *n_kept,
+                         float *t_final, unsigned *n_frag, cudaStream_t stream);
+cudaError_t launch_backward(const Frame &F, const Workspace &W, long long n, const float4 *rec,
+                            const float *opacity, const void *desc, int desc_dtype, const unsigned *kept,
+                            const unsigned char *n_kept, const float *grad_pyramid, float *grad_pos,
+                            float *grad_sw, float *grad_opacity, float *grad_desc, cudaStream_t stream);
+
+}  // namespace tpk

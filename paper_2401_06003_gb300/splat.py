@@ -1,0 +1,196 @@
+"""Thin torch layer over the C ABI: device buffers, streams and autograd.
+
+Every step of the splatting path (projection, binning, per-pixel top-K,
+blending and the adjoint) runs inside libtrips.so; this module only
+allocates tensors, passes their pointers and the current CUDA stream, and
+wires the backward call into ``torch.autograd``.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+
+import torch
+
+from . import _lib
+
+_DTYPES = {torch.float32: _lib.TP_F32, torch.bfloat16: _lib.TP_BF16}
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _need(t, dtype, shape, name, device):
+    if t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous() or t.device != device:
+        raise ValueError(f"{name}: expected contiguous {dtype} {tuple(shape)} on {device}, "
+                         f"got {t.dtype} {tuple(t.shape)} on {t.device}")
+
+
+@dataclasses.dataclass
+class Frame:
+    """Outputs of one forward render and what the backward pass needs."""
+
+    pyramid: torch.Tensor       # [P, D] float32
+    records: torch.Tensor       # [n, 4] float32 (x, y, z, s)
+    workspace: torch.Tensor     # uint8, holds the frame's tile lists
+    kept: torch.Tensor | None = None      # [P, K] int32 view of uint32 ids
+    n_kept: torch.Tensor | None = None    # [P] uint8
+    t_final: torch.Tensor | None = None   # [P] float32
+    n_frag: torch.Tensor | None = None    # [P] int32 view of uint32 counts
+
+
+class Renderer:
+    """A camera plus render settings; renders point clouds through libtrips.so.
+
+    ``mode``: "recompute" keeps only the tile lists between the forward and
+    the backward pass and rebuilds each pixel's sorted list in the backward
+    kernel; "store" keeps the per-pixel kept lists from the forward pass.
+    """
+
+    def __init__(self, camera, n_layers: int, K: int = 16, D: int = 4, eps: float = 0.25,
+                 desc_dtype=torch.float32, mode: str = "recompute", tile=(16, 16), device=None):
+        self.lib = _lib.load()
+        self.camera = camera
+        self.cam = _lib.make_camera(camera)
+        if desc_dtype not in _DTYPES:
+            raise ValueError(f"descriptor dtype {desc_dtype} not supported")
+        self.desc_dtype = desc_dtype
+        self.mode = {"store": _lib.TP_STORE_LISTS, "recompute": _lib.TP_RECOMPUTE}[mode]
+        self.cfg = _lib.make_config(n_layers, K, D, eps, _DTYPES[desc_dtype], self.mode, tile[0], tile[1])
+        self.n_layers, self.K, self.D = int(n_layers), int(K), int(D)
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        offs = (ctypes.c_int64 * (n_layers + 1))()
+        P = self.lib.tp_pyramid_pixels(ctypes.byref(self.cam), n_layers, offs)
+        if P < 0:
+            raise ValueError("invalid camera or layer count")
+        self.P = int(P)
+        self.layer_offsets = [int(v) for v in offs]
+
+    # -- sizes ---------------------------------------------------------------
+    def workspace_bytes(self, n: int, capacity: int = 0) -> int:
+        b = self.lib.tp_workspace_bytes(ctypes.byref(self.cfg), ctypes.byref(self.cam), int(n), int(capacity))
+        if b < 0:
+            raise ValueError("invalid configuration for the workspace")
+        return int(b)
+
+    def new_workspace(self, n: int, capacity: int = 0) -> torch.Tensor:
+        ws = torch.empty(self.workspace_bytes(n, capacity), dtype=torch.uint8, device=self.device)
+        assert ws.data_ptr() % 256 == 0
+        return ws
+
+    def layer(self, pyramid: torch.Tensor, L: int) -> torch.Tensor:
+        """View of layer L of a [P, D] pyramid as [H_L, W_L, D]."""
+        s = 1 << L
+        w = -(-self.cam.width // s)
+        h = -(-self.cam.height // s)
+        return pyramid[self.layer_offsets[L]:self.layer_offsets[L + 1]].view(h, w, -1)
+
+    # -- the four C-ABI stages -----------------------------------------------
+    def project(self, pos, size_w, ws, records=None):
+        n = pos.shape[0]
+        _need(pos, torch.float32, (n, 3), "pos", self.device)
+        _need(size_w, torch.float32, (n,), "size_w", self.device)
+        if records is None:
+            records = torch.empty((n, 4), dtype=torch.float32, device=self.device)
+        st = self.lib.tp_project(ctypes.byref(self.cfg), ctypes.byref(self.cam), n, _ptr(pos), _ptr(size_w),
+                                 _ptr(records), _ptr(ws), ws.numel(), _stream(self.device))
+        _lib.check("tp_project", st)
+        return records
+
+    def splat_forward(self, records, ws):
+        st = self.lib.tp_splat_forward(ctypes.byref(self.cfg), ctypes.byref(self.cam), records.shape[0],
+                                       _ptr(records), _ptr(ws), ws.numel(), _stream(self.device))
+        _lib.check("tp_splat_forward", st)
+
+    def blend(self, records, opacity, desc, ws, store_lists=False, stats=False, pyramid=None):
+        n = records.shape[0]
+        _need(opacity, torch.float32, (n,), "opacity", self.device)
+        _need(desc, self.desc_dtype, (n, self.D), "desc", self.device)
+        dev = self.device
+        if pyramid is None:
+            pyramid = torch.empty((self.P, self.D), dtype=torch.float32, device=dev)
+        kept = n_kept = t_final = n_frag = None
+        if store_lists or stats:
+            kept = torch.empty((self.P, self.K), dtype=torch.int32, device=dev)
+            n_kept = torch.empty((self.P,), dtype=torch.uint8, device=dev)
+        if stats:
+            t_final = torch.empty((self.P,), dtype=torch.float32, device=dev)
+            n_frag = torch.empty((self.P,), dtype=torch.int32, device=dev)
+        st = self.lib.tp_blend(ctypes.byref(self.cfg), ctypes.byref(self.cam), n, _ptr(records), _ptr(opacity),
+                               _ptr(desc), _ptr(pyramid), _ptr(kept), _ptr(n_kept), _ptr(t_final), _ptr(n_frag),
+                               _ptr(ws), ws.numel(), _stream(dev))
+        _lib.check("tp_blend", st)
+        return pyramid, kept, n_kept, t_final, n_frag
+
+    def splat_backward(self, records, opacity, desc, grad_pyramid, ws, kept=None, n_kept=None, grads=None):
+        n = records.shape[0]
+        dev = self.device
+        _need(grad_pyramid, torch.float32, (self.P, self.D), "grad_pyramid", dev)
+        if grads is None:
+            grads = (torch.empty((n, 3), dtype=torch.float32, device=dev),
+                     torch.empty((n,), dtype=torch.float32, device=dev),
+                     torch.empty((n,), dtype=torch.float32, device=dev),
+                     torch.empty((n, self.D), dtype=torch.float32, device=dev))
+        gp, gs, go, gd = grads
+        st = self.lib.tp_splat_backward(ctypes.byref(self.cfg), ctypes.byref(self.cam), n, _ptr(records),
+                                        _ptr(opacity), _ptr(desc), _ptr(kept), _ptr(n_kept), _ptr(grad_pyramid),
+                                        _ptr(gp), _ptr(gs), _ptr(go), _ptr(gd), _ptr(ws), ws.numel(), _stream(dev))
+        _lib.check("tp_splat_backward", st)
+        return grads
+
+    def status(self, ws) -> int:
+        """Synchronises the current stream and returns the TP_FLAG_* bits of the frame."""
+        flags = ctypes.c_int32(0)
+        st = self.lib.tp_get_status(_ptr(ws), _stream(self.device), ctypes.byref(flags))
+        if st == _lib.TP_ERR_CUDA or st == _lib.TP_ERR_INVALID_ARG:
+            _lib.check("tp_get_status", st)
+        return int(flags.value)
+
+    # -- whole frames --------------------------------------------------------
+    def render(self, pos, size_w, opacity, desc, store_lists=None, stats=False, ws=None) -> Frame:
+        """Forward render: project, splat, blend."""
+        n = pos.shape[0]
+        if store_lists is None:
+            store_lists = self.mode == _lib.TP_STORE_LISTS
+        if ws is None:
+            ws = self.new_workspace(n)
+        records = self.project(pos, size_w, ws)
+        self.splat_forward(records, ws)
+        pyramid, kept, n_kept, t_final, n_frag = self.blend(records, opacity, desc, ws, store_lists, stats)
+        return Frame(pyramid, records, ws, kept, n_kept, t_final, n_frag)
+
+    def backward(self, frame: Frame, opacity, desc, grad_pyramid):
+        """Gradients (pos, size_w, opacity, desc) of sum(grad_pyramid * pyramid) for a rendered frame."""
+        use_lists = self.mode == _lib.TP_STORE_LISTS and frame.kept is not None
+        return self.splat_backward(frame.records, opacity, desc, grad_pyramid.contiguous(), frame.workspace,
+                                   frame.kept if use_lists else None, frame.n_kept if use_lists else None)
+
+
+class TripsSplat(torch.autograd.Function):
+    """pyramid = Phi(camera; pos, size_w, opacity, desc) with the hand-written adjoint."""
+
+    @staticmethod
+    def forward(ctx, pos, size_w, opacity, desc, renderer: Renderer):
+        frame = renderer.render(pos.detach(), size_w.detach(), opacity.detach(), desc.detach())
+        ctx.renderer = renderer
+        ctx.frame = frame
+        ctx.save_for_backward(opacity, desc)
+        return frame.pyramid
+
+    @staticmethod
+    def backward(ctx, grad_pyramid):
+        opacity, desc = ctx.saved_tensors
+        gp, gs, go, gd = ctx.renderer.backward(ctx.frame, opacity.detach(), desc.detach(),
+                                                grad_pyramid.to(torch.float32))
+        ctx.frame = None
+        return gp, gs, go, gd.to(desc.dtype), None
+
+
+def splat(pos, size_w, opacity, desc, renderer: Renderer) -> torch.Tensor:
+    """Differentiable trilinear point splatting into a [P, D] feature pyramid."""
+    return TripsSplat.apply(pos, size_w, opacity, desc, renderer)

@@ -1,0 +1,66 @@
+"""The C-ABI library builds, loads and exports every declared symbol; host-only logic.
+
+Nothing here launches a kernel: the calls exercised are the pure host
+functions (layout, workspace size, argument checks that fail before any
+CUDA call) and the status strings.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2401_06003_gb300 import _lib, scenes
+from paper_2401_06003_gb300.build import build
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build()
+    return _lib.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _lib.header_functions()
+    assert {"tp_project", "tp_splat_forward", "tp_blend", "tp_splat_backward"} <= set(names)
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(_lib._SIGS) == set(names), "binding and header disagree"
+    assert lib.tp_version() >= 100
+
+
+def test_struct_layout_matches_header():
+    assert ctypes.sizeof(_lib.tp_camera) == 17 * 4 + 2 * 4
+    assert ctypes.sizeof(_lib.tp_config) == 8 * 4
+
+
+@pytest.mark.parametrize("W,H,L", [(256, 256, 4), (1920, 1080, 8), (257, 131, 3), (3840, 2160, 10), (1, 1, 1)])
+def test_pyramid_pixels_matches_oracle_layout(lib, W, H, L):
+    cam = scenes.Camera(W, W, W / 2, H / 2, np.eye(3), np.zeros(3), W, H)
+    offs = (ctypes.c_int64 * (L + 1))()
+    P = lib.tp_pyramid_pixels(ctypes.byref(_lib.make_camera(cam)), L, offs)
+    ref, _, _ = oracle.pyramid_layout(W, H, L)
+    assert P == ref[-1]
+    assert list(offs) == ref.tolist()
+
+
+def test_workspace_bytes_and_checks(lib):
+    cam = _lib.make_camera(scenes.make_config("cube20k_256", n=10).camera)
+    cfg = _lib.make_config(4, 16, 4)
+    b8 = lib.tp_workspace_bytes(ctypes.byref(cfg), ctypes.byref(cam), 1000, 0)
+    b1 = lib.tp_workspace_bytes(ctypes.byref(cfg), ctypes.byref(cam), 1000, 1000)
+    assert b8 > b1 > 0 and (b8 - b1) >= 7000 * 20 - 512
+    bad = _lib.make_config(4, 12, 4)  # K = 12 is not instantiated
+    assert lib.tp_workspace_bytes(ctypes.byref(bad), ctypes.byref(cam), 10, 0) == -1
+    bad = _lib.make_config(0, 16, 4)
+    assert lib.tp_workspace_bytes(ctypes.byref(bad), ctypes.byref(cam), 10, 0) == -1
+    # argument errors come back before any CUDA call
+    st = lib.tp_project(ctypes.byref(cfg), ctypes.byref(cam), 10, None, None, None, None, 0, None)
+    assert st == _lib.TP_ERR_INVALID_ARG
+    st = lib.tp_project(ctypes.byref(_lib.make_config(4, 12, 4)), ctypes.byref(cam), 10, None, None, None,
+                        None, 0, None)
+    assert st == _lib.TP_ERR_UNSUPPORTED
+    cam.znear = 0.0
+    st = lib.tp_splat_forward(ctypes.byref(cfg), ctypes.byref(cam), 10, None, None, 0, None)
+    assert st == _lib.TP_ERR_INVALID_ARG
+    assert lib.tp_status_string(_lib.TP_ERR_CAPACITY).decode().startswith("workspace")

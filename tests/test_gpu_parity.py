@@ -1,0 +1,291 @@
+"""Parity of the CUDA path (through the C ABI) with the float64 oracle.
+
+Membership, order and counts are compared bit-exactly; pyramid values,
+transmittance and gradients within the stated tolerances.  Every input is
+seeded and synthetic (paper_2401_06003_gb300.scenes).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from gpu_helpers import (BF16_RTOL, GRAD_RTOL, PYR_RTOL, assert_close_scaled, compare_forward, compare_grads,
+                         compare_records, device, gpu_frame, to_dev)
+from paper_2401_06003_gb300 import Renderer, scenes, splat
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle(scene, view=0, prec32=True, desc=None, **kw):
+    return oracle.Frame.from_scene(scene, view=view, prec32=prec32, desc=desc, **kw)
+
+
+@pytest.fixture(scope="module")
+def cube():
+    return scenes.make_config("cube20k_256")
+
+
+# ---------------------------------------------------------------------------
+# Forward
+# ---------------------------------------------------------------------------
+
+def test_cube_forward_exact_lists(cube):
+    r, fr, _, out = gpu_frame(cube)
+    ofr = _oracle(cube)
+    compare_records(out["records"], ofr)
+    ref = ofr.render()
+    assert (ref["n_frag"] > cube.K).any(), "the workload must exercise the K cap"
+    compare_forward(out, ref, r.layer_offsets, name="cube20k")
+    assert out["flags"] == 0
+
+
+def test_cube_forward_deterministic(cube):
+    _, _, _, a = gpu_frame(cube)
+    _, _, _, b = gpu_frame(cube)
+    for k in ("pyramid", "kept", "t_final", "n_frag"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_hand_examples_on_gpu(golden_dir):
+    with open(os.path.join(golden_dir, "hand_examples.json")) as fh:
+        examples = json.load(fh)["examples"]
+    for ex in examples:
+        cam = ex["camera"]
+        camera = scenes.Camera(cam[0], cam[1], cam[2], cam[3], np.array(cam[4:13]).reshape(3, 3),
+                               np.array(cam[13:16]), ex["width"], ex["height"], cam[16])
+        pts = ex["points"]
+        sc = scenes.Scene(ex["name"], np.array([p["pos"] for p in pts], np.float32),
+                          np.array([p["size_w"] for p in pts], np.float32),
+                          np.array([p["desc"] for p in pts], np.float32),
+                          np.array([p["opacity"] for p in pts], np.float32), [camera], ex["n_layers"], ex["K"])
+        _, _, _, out = gpu_frame(sc)
+        if "screen" in ex:
+            np.testing.assert_array_equal(out["records"], np.array(ex["screen"], np.float32))
+        for px in ex["pixels"]:
+            np.testing.assert_allclose(out["pyramid"][px["pixel"]], px["C"], rtol=1e-6, atol=1e-7, err_msg=ex["name"])
+            np.testing.assert_allclose(out["t_final"][px["pixel"]], px["T_final"], rtol=1e-6, atol=1e-7)
+            if "kept" in px:
+                nk = out["n_kept"][px["pixel"]]
+                assert out["kept"][px["pixel"], :nk].tolist() == px["kept"]
+        if "fragments" in ex:
+            assert out["n_frag"].sum() == len(ex["fragments"])
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (32, 8), (8, 8), (13, 7)])
+@pytest.mark.parametrize("K", [4, 8, 16, 32])
+def test_ragged_image_tiles_and_caps(tile, K):
+    sc = scenes.scene_uniform_cube(n=4000, seed=5, res=64)
+    cam = scenes.Camera(150.0, 150.0, 128.5, 65.5, np.eye(3), np.array([0.0, 0.0, 3.0]), 257, 131)
+    sc.cameras = [cam]
+    sc.n_layers = 5
+    sc.K = K
+    r, fr, _, out = gpu_frame(sc, tile=tile)
+    ofr = _oracle(sc)
+    compare_records(out["records"], ofr)
+    compare_forward(out, ofr.render(), r.layer_offsets, name=f"tile{tile} K{K}")
+
+
+def test_dense_pixel_cap_and_ties():
+    """Many points in one pixel, with equal depths: the first K by (z, index)."""
+    W = H = 32
+    f, z = 32.0, 2.0
+    n = 300
+    rng = np.random.default_rng(9)
+    x = 16.5 + rng.uniform(-0.2, 0.2, n)
+    y = 16.5 + rng.uniform(-0.2, 0.2, n)
+    zz = np.where(rng.uniform(size=n) < 0.5, z, rng.choice([1.5, 2.5, 3.0], n))  # many exact ties
+    pos = np.stack([(x - W / 2) * zz / f, (y - H / 2) * zz / f, zz], 1).astype(np.float32)
+    sw = (rng.uniform(0.2, 3.0, n) * zz / f).astype(np.float32)
+    cam = scenes.Camera(f, f, W / 2, H / 2, np.eye(3), np.zeros(3), W, H)
+    sc = scenes.Scene("dense", pos, sw, rng.uniform(0, 1, (n, 4)).astype(np.float32),
+                      rng.uniform(0.05, 0.3, n).astype(np.float32), [cam], 3, 16)
+    r, _, _, out = gpu_frame(sc)
+    ofr = _oracle(sc)
+    ref = ofr.render()
+    assert ref["n_frag"].max() > 100
+    compare_records(out["records"], ofr)
+    compare_forward(out, ref, r.layer_offsets, name="dense")
+
+
+def test_empty_and_single_point():
+    cam = scenes.Camera(64.0, 64.0, 32, 32, np.eye(3), np.array([0, 0, 2.0]), 64, 64)
+    for n in (0, 1):
+        rng = np.random.default_rng(n)
+        sc = scenes.Scene("tiny", rng.uniform(-0.5, 0.5, (n, 3)).astype(np.float32),
+                          np.full(n, 0.05, np.float32), rng.uniform(0, 1, (n, 4)).astype(np.float32),
+                          np.full(n, 0.5, np.float32), [cam], 4, 16)
+        r, fr, ins, out = gpu_frame(sc)
+        compare_forward(out, _oracle(sc).render(), r.layer_offsets, name=f"n={n}")
+        if n == 0:
+            assert np.all(out["pyramid"] == 0) and np.all(out["t_final"] == 1)
+        g = r.splat_backward(fr.records, ins[2], ins[3], torch.ones_like(fr.pyramid), fr.workspace)
+        assert all(t.shape[0] == n for t in g)
+
+
+def test_culled_and_nonfinite_points(cube):
+    sc = cube.subset(np.arange(2000))
+    pos = sc.pos.copy()
+    pos[0] = [0.0, 0.0, -10.0]          # behind the camera
+    pos[1] = [np.nan, 0.0, 0.0]         # non-finite
+    pos[2] = [0.0, np.inf, 0.0]
+    sc.pos = pos
+    sw = sc.size_w.copy()
+    sw[3] = -1.0                        # negative size
+    sc.size_w = sw
+    r, _, _, out = gpu_frame(sc)
+    from paper_2401_06003_gb300 import _lib
+    assert out["flags"] & _lib.TP_FLAG_NONFINITE
+    assert np.all(out["records"][:4] == 0)
+    ofr = _oracle(sc)
+    assert ofr.n_bad == 3
+    compare_forward(out, ofr.render(), r.layer_offsets, name="culled")
+
+
+def test_capacity_overflow_is_reported(cube):
+    from paper_2401_06003_gb300 import _lib
+    _, _, _, out = gpu_frame(cube, capacity=1000)
+    assert out["flags"] & _lib.TP_FLAG_CAPACITY
+    _, _, _, out = gpu_frame(cube)
+    assert not (out["flags"] & _lib.TP_FLAG_CAPACITY)
+
+
+def test_bf16_descriptors(cube):
+    D = 16
+    rng = np.random.default_rng(4)
+    desc32 = rng.uniform(0, 1, (cube.n, D)).astype(np.float32)
+    desc_bf = torch.from_numpy(desc32).to(torch.bfloat16)
+    desc_rounded = desc_bf.to(torch.float32).numpy()
+    r, _, _, out = gpu_frame(cube, desc=desc32, desc_dtype=torch.bfloat16)
+    # against the oracle on the bf16 values: float32-level agreement
+    ref_b = _oracle(cube, desc=desc_rounded).render()
+    compare_forward(out, ref_b, r.layer_offsets, name="bf16 vs oracle(bf16 values)")
+    # against the oracle on the original float32 descriptors
+    ref_f = _oracle(cube, desc=desc32).render()
+    segs = [(r.layer_offsets[L], r.layer_offsets[L + 1]) for L in range(cube.n_layers)]
+    assert_close_scaled(out["pyramid"], ref_f["pyramid"], BF16_RTOL, name="bf16 vs oracle(f32)", segments=segs)
+
+
+# ---------------------------------------------------------------------------
+# Backward
+# ---------------------------------------------------------------------------
+
+def _gpu_grads(r, fr, ins, G, store):
+    gp, gs, go, gd = r.splat_backward(fr.records, ins[2], ins[3], to_dev(G), fr.workspace,
+                                      fr.kept if store else None, fr.n_kept if store else None)
+    return dict(pos=gp.cpu().numpy(), size_w=gs.cpu().numpy(), opacity=go.cpu().numpy(), desc=gd.cpu().numpy())
+
+
+@pytest.mark.parametrize("store", [True, False])
+def test_cube_backward_vs_oracle_adjoint(cube, store):
+    r, fr, ins, out = gpu_frame(cube, mode="store" if store else "recompute")
+    ofr = _oracle(cube)
+    G = np.random.default_rng(21).uniform(-1, 1, (r.P, cube.D))
+    ref = ofr.backward(G)
+    got = _gpu_grads(r, fr, ins, G.astype(np.float32), store)
+    compare_grads(got, ref, name="cube20k")
+
+
+def test_stored_and_recomputed_lists_agree(cube):
+    r, fr, ins, _ = gpu_frame(cube)
+    G = np.random.default_rng(22).uniform(-1, 1, (r.P, cube.D)).astype(np.float32)
+    a = _gpu_grads(r, fr, ins, G, True)
+    b = _gpu_grads(r, fr, ins, G, False)
+    for k in a:
+        assert_close_scaled(a[k], b[k], 1e-5, name=k)
+
+
+def test_autograd_function_matches_oracle(cube):
+    sc = cube.subset(np.arange(5000))
+    r = Renderer(sc.camera, sc.n_layers, K=sc.K, D=sc.D, mode="recompute", device=device())
+    pos = to_dev(sc.pos).requires_grad_(True)
+    sw = to_dev(sc.size_w).requires_grad_(True)
+    op = to_dev(sc.opacity).requires_grad_(True)
+    desc = to_dev(sc.desc).requires_grad_(True)
+    G = np.random.default_rng(23).uniform(-1, 1, (r.P, sc.D))
+    pyr = splat(pos, sw, op, desc, r)
+    (pyr * to_dev(G)).sum().backward()
+    ref = _oracle(sc).backward(G)
+    got = dict(pos=pos.grad.cpu().numpy(), size_w=sw.grad.cpu().numpy(), opacity=op.grad.cpu().numpy(),
+               desc=desc.grad.cpu().numpy())
+    compare_grads(got, ref, name="autograd")
+
+
+def _pixels_by_point(pix, idx):
+    """Function point -> sorted pyramid pixels of its fragments."""
+    order = np.lexsort((pix, idx))
+    ps, ids = pix[order], idx[order]
+
+    def lookup(p):
+        a, b = np.searchsorted(ids, p, "left"), np.searchsorted(ids, p, "right")
+        return ps[a:b]
+    return lookup
+
+
+def test_spheres_gradients_vs_finite_differences():
+    """1M points at 1920x1080, 8 layers: every gradient against the oracle adjoint,
+    and a 1k-point subset against float64 central differences."""
+    sc = scenes.make_config("spheres1m_1080p")
+    r, fr, ins, out = gpu_frame(sc, mode="recompute")
+    o32 = _oracle(sc)
+    compare_records(out["records"], o32)
+    ref = o32.render()
+    compare_forward(out, ref, r.layer_offsets, name="spheres1m")
+    G = np.random.default_rng(31).uniform(-1, 1, (r.P, sc.D))
+    got = _gpu_grads(r, fr, ins, G.astype(np.float32), False)
+    compare_grads(got, o32.backward(G), name="spheres1m")
+    # float64 central differences on 1000 visible points whose discrete state
+    # (pixels and kept order) is the same in float32 and float64
+    o64 = _oracle(sc, prec32=False)
+    rng = np.random.default_rng(32)
+    visible = np.flatnonzero(out["records"][:, 2] > 0)
+    cand = rng.choice(visible, size=1500, replace=False)
+    by32 = _pixels_by_point(*o32.fragments()[::2])
+    by64 = _pixels_by_point(*o64.fragments()[::2])
+    ref64 = o64.render()
+    same = []
+    for p in cand:
+        a, b = by32(p), by64(p)
+        if a.size and np.array_equal(a, b) and np.array_equal(ref["kept"][a], ref64["kept"][a]):
+            same.append(p)
+        if len(same) == 1000:
+            break
+    same = np.array(same)
+    assert same.size == 1000
+    fd, valid = o64.finite_differences(G, same)
+    gpu = np.concatenate([got["pos"][same], got["size_w"][same, None], got["opacity"][same, None],
+                          got["desc"][same]], 1)
+    assert valid.mean() > 0.95
+    for c, name in enumerate(["X", "Y", "Z", "s_w", "alpha"] + [f"tau{d}" for d in range(sc.D)]):
+        v = valid[:, c]
+        assert_close_scaled(gpu[v, c], fd[v, c], GRAD_RTOL, name=f"fd {name}")
+
+
+# ---------------------------------------------------------------------------
+# Full-size scene-shaped workload, in the configuration the benchmark times
+# ---------------------------------------------------------------------------
+
+def test_ground6m_full_size_sampled():
+    sc = scenes.make_config("ground6m_1080p")
+    r, fr, ins, out = gpu_frame(sc, mode="recompute")
+    assert out["flags"] == 0
+    rng = np.random.default_rng(41)
+    # records: a sample of points, bit-exact
+    pts = rng.choice(sc.n, size=200_000, replace=False)
+    sub = sc.subset(pts)
+    compare_records(out["records"][pts], _oracle(sub))
+    # forward: 20k sampled pixels over all layers, plus the pixels of 2k points
+    vis = np.flatnonzero(out["records"][:, 2] > 0)
+    sel_pts = rng.choice(vis, size=2000, replace=False)
+    pix = rng.choice(r.P, size=20_000, replace=False)
+    ofr = _oracle(sc, pixels=pix, points=sel_pts)
+    rows = ofr.pixels()
+    compare_forward(out, ofr.render(), r.layer_offsets, rows=rows, name="ground6m sampled")
+    # backward: gradients of the 2k points are exact in a frame that covers all their pixels
+    G = rng.uniform(-1, 1, (r.P, sc.D)).astype(np.float32)
+    got = _gpu_grads(r, fr, ins, G, False)
+    ref = ofr.backward(G[rows].astype(np.float64))
+    compare_grads({k: v[sel_pts] for k, v in got.items()}, {k: v[sel_pts] for k, v in ref.items()},
+                  name="ground6m sampled")
