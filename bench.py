@@ -44,6 +44,7 @@ def parse_args():
     ap.add_argument("--workload", default="ground6m_1080p")
     ap.add_argument("--mode", choices=["recompute", "store"], default="recompute")
     ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--points", type=int, default=0, help="override the workload's point count (profiling)")
     ap.add_argument("--ref-sample", type=int, default=2_000_000, help="points per reference-arm step")
     ap.add_argument("--cpu-frames", type=int, default=2, help="full oracle frames timed for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -221,7 +222,7 @@ def run_ours(args):
     build_lib()
     rank, world, local = dist_setup(True)
     dev = torch.device("cuda", local)
-    sc = scenes.make_config(args.workload)
+    sc = scenes.make_config(args.workload, n=args.points or None)
     tw, th = (int(v) for v in args.tile.split("x"))
     desc_dtype = torch.bfloat16 if args.workload.endswith("bf16") else torch.float32
     r = Renderer(sc.camera, sc.n_layers, K=sc.K, D=sc.D, desc_dtype=desc_dtype, mode=args.mode, tile=(tw, th),

@@ -189,10 +189,10 @@ class Frame:
     def finite_differences(self, G, points, h_pos=1e-6, h_sw_rel=1e-6, h_alpha=1e-6, h_desc=1e-3):
         """Local central differences for the given points: (fd [m, 5+D], valid [m, 5+D]).
 
-        Columns: X, Y, Z, s_w, alpha, desc[0..D).  Needs ``prec32=False``.
+        Columns: X, Y, Z, s_w, alpha, desc[0..D).  In a ``prec32`` frame the
+        differences are float64 changes around the frame's float32
+        screen-space state (the state its integer decisions were taken at).
         """
-        if self.prec32:
-            raise ValueError("finite differences need a float64 frame (prec32=False)")
         G = np.ascontiguousarray(G, np.float64).reshape(self.n_pix, self.D)
         pts = np.ascontiguousarray(np.asarray(points, np.int64))
         fd = np.zeros((pts.size, 5 + self.D), np.float64)

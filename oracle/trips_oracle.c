@@ -681,6 +681,39 @@ typedef struct {
     double loss;
 } olocal;
 
+/* Screen-space state of point p for perturbed inputs.  A float64 frame
+ * projects them in float64.  A float32 frame keeps its float32 screen-space
+ * state and adds the float64 change of the projection, so the differences
+ * are taken around exactly the state the frame's decisions were made at. */
+static void eval_proj(const oframe *fr, int64_t p, const double *pos3, double sw, oproj *o)
+{
+    if (!fr->prec32) {
+        project_point64(&fr->cam, pos3, sw, o);
+        return;
+    }
+    const double base3[3] = {fr->pos[3 * p], fr->pos[3 * p + 1], fr->pos[3 * p + 2]};
+    oproj b64, q64;
+    project_point64(&fr->cam, base3, (double)fr->sw[p], &b64);
+    project_point64(&fr->cam, pos3, sw, &q64);
+    *o = fr->proj[p];
+    if (!o->vis || !b64.vis || !q64.vis) {
+        o->vis = 0;
+        return;
+    }
+    o->x += q64.x - b64.x;
+    o->y += q64.y - b64.y;
+    o->z += q64.z - b64.z;
+    o->s += q64.s - b64.s;
+}
+
+static int same_taps(const ofrag *a, int na, const ofrag *b, int nb)
+{
+    if (na != nb) return 0;
+    for (int t = 0; t < na; ++t)
+        if (a[t].layer != b[t].layer || a[t].j != b[t].j || a[t].k != b[t].k) return 0;
+    return 1;
+}
+
 static int local_eval(const oframe *fr, int64_t p, const double *pos3, double sw, double alpha,
                       const double *desc, const double *G, olocal *out)
 {
@@ -688,7 +721,7 @@ static int local_eval(const oframe *fr, int64_t p, const double *pos3, double sw
     ofrag frs[8];
     int D = fr->D, K = fr->K;
     if (K > ORC_FD_MAXK) return -1;
-    project_point64(&fr->cam, pos3, sw, &o);
+    eval_proj(fr, p, pos3, sw, &o);
     int nf = point_fragments(&o, &fr->ly, 0, fr->eps, frs);
     out->n = nf;
     out->loss = 0.0;
@@ -745,15 +778,15 @@ static int same_state(const olocal *a, const olocal *b)
  * s_w (step h_sw_rel * s_w), alpha (step h_alpha), desc[0..D) (step
  * h_desc).  fd is [n_sel, 5 + D]; valid is 1 where the discrete state is
  * identical at -h, 0 and +h (else the entry is 0 and not a derivative).
- * Needs a float64 frame that covers every pixel of the selected points.
- * Returns 0, or -1 for a float32 frame or bad arguments.
+ * The frame must cover every pixel of the selected points.  In a float32
+ * frame the differences are taken around the frame's float32 screen-space
+ * state (see eval_proj).  Returns 0, or -1 on bad arguments.
  */
 int orc_frame_fd(const oframe *fr, const double *G, int64_t n_sel, const int64_t *sel, double h_pos,
                  double h_sw_rel, double h_alpha, double h_desc, double *fd, int8_t *valid)
 {
     int D = fr->D;
     int np = 5 + D;
-    if (fr->prec32) return -1;
     double *d0 = (double *)malloc((size_t)D * sizeof(double));
     double *dv = (double *)malloc((size_t)D * sizeof(double));
     if (!d0 || !dv) { free(d0); free(dv); return -1; }
@@ -766,6 +799,15 @@ int orc_frame_fd(const oframe *fr, const double *G, int64_t n_sel, const int64_t
         for (int d = 0; d < D; ++d) d0[d] = fr->desc[(int64_t)D * p + d];
         olocal base, plus, minus;
         if (local_eval(fr, p, pos0, sw0, a0, d0, G, &base) != 0) continue;
+        {
+            /* the unperturbed local state must be the frame's own state */
+            ofrag mine[8], here[8];
+            oproj o;
+            int nm = point_fragments(&fr->proj[p], &fr->ly, fr->prec32, fr->eps, mine);
+            eval_proj(fr, p, pos0, sw0, &o);
+            int nh = point_fragments(&o, &fr->ly, 0, fr->eps, here);
+            if (!same_taps(mine, nm, here, nh)) continue;
+        }
         for (int k = 0; k < np; ++k) {
             double h = k < 3 ? h_pos : k == 3 ? h_sw_rel * sw0 : k == 4 ? h_alpha : h_desc;
             double lp = 0.0, lm = 0.0;

@@ -107,7 +107,9 @@ int64_t capacity_for(const Frame &F, int64_t ws_bytes)
 {
     const WsLayout w0 = layout_for(F, 0);
     if (ws_bytes < w0.end) return -1;
-    int64_t c = (ws_bytes - w0.end - 2 * kAlign) / 20;
+    // align_up only adds bytes, so (ws_bytes - idx) / 20 is an upper bound;
+    // alignment costs < 256 bytes, so the loop runs at most ~13 times.
+    int64_t c = (ws_bytes - w0.idx) / 20;
     if (c < 0) c = 0;
     while (c > 0 && layout_for(F, c).end > ws_bytes) --c;
     if (c > 0x7FFFFFFF) c = 0x7FFFFFFF;

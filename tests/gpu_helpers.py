@@ -25,8 +25,10 @@ def to_dev(a, dtype=torch.float32):
 
 
 def gpu_frame(scene, view=0, K=None, mode="store", tile=(16, 16), desc_dtype=torch.float32, desc=None,
-              capacity=0, pos=None):
-    """Render one view on the GPU with every optional output; numpy results."""
+              capacity=0, pos=None, expect_flags=0):
+    """Render one view on the GPU with every optional output; numpy results.
+
+    The device status flags must equal ``expect_flags`` (None: not checked)."""
     cam = scene.cameras[view]
     K = K or scene.K
     d = scene.desc if desc is None else desc
@@ -48,6 +50,8 @@ def gpu_frame(scene, view=0, K=None, mode="store", tile=(16, 16), desc_dtype=tor
         n_frag=fr.n_frag.cpu().numpy(),
         flags=flags,
     )
+    if expect_flags is not None:
+        assert flags == expect_flags, f"device status flags {flags:#x}, expected {expect_flags:#x}"
     return r, fr, (t_pos, t_sw, t_op, t_desc), out
 
 
@@ -74,9 +78,7 @@ def assert_close_scaled(got, ref, rtol, floor=FLOOR, name="", segments=None):
 def compare_forward(out, ofr_out, layer_offsets, rtol=PYR_RTOL, rows=None, name=""):
     """Element-wise: kept ids, n_kept and n_frag exact; pyramid and T_final within rtol."""
     sel = slice(None) if rows is None else rows
-    kept = out["kept"][sel].astype(np.int64)
-    kept[kept == 0xFFFFFFFF] = -1
-    kept[kept == -1] = -1
+    kept = out["kept"][sel].astype(np.int64)  # uint32 ids read as int32: 0xFFFFFFFF is -1
     np.testing.assert_array_equal(out["n_frag"][sel].astype(np.int64), ofr_out["n_frag"], err_msg=f"{name} n_frag")
     np.testing.assert_array_equal(out["n_kept"][sel], ofr_out["n_kept"], err_msg=f"{name} n_kept")
     np.testing.assert_array_equal(kept, ofr_out["kept"].astype(np.int64), err_msg=f"{name} kept lists")

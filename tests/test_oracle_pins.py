@@ -362,3 +362,23 @@ def test_adjoint_matches_finite_differences(seed):
     # points with no fragment have zero gradient
     _, vis = fr.records()
     assert np.all(ad[vis == 0] == 0)
+
+
+def test_float32_frame_adjoint_matches_anchored_differences():
+    """In a float32 frame, the adjoint equals float64 differences taken around
+    the frame's own float32 screen-space state."""
+    rng = np.random.default_rng(7)
+    n, W, H, n_layers, K, D = 80, 640, 360, 6, 4, 3
+    pos = np.stack([rng.uniform(-0.9, 0.9, n), rng.uniform(-0.5, 0.5, n), rng.uniform(1.0, 3.0, n)], 1)
+    pos = pos.astype(np.float32)
+    sw = np.exp(rng.uniform(math.log(1e-3), math.log(0.05), n)).astype(np.float32)
+    alpha = rng.uniform(0.1, 0.95, n).astype(np.float32)
+    desc = rng.uniform(-1, 1, (n, D)).astype(np.float32)
+    fr = oracle.Frame(_cam(360.0, W, H), W, H, n_layers, K, pos, sw, alpha, desc, prec32=True)
+    G = rng.uniform(-1, 1, (fr.n_pix, D))
+    g = fr.backward(G)
+    fd, valid = fr.finite_differences(G, np.arange(n))
+    ad = np.concatenate([g["pos"], g["size_w"][:, None], g["opacity"][:, None], g["desc"]], 1)
+    assert valid.mean() > 0.9
+    err = np.abs(ad - fd)[valid]
+    assert err.max() <= 1e-6 * np.abs(fd[valid]).max(), err.max()
