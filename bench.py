@@ -251,10 +251,10 @@ def run_ours(args):
         r.project(pos, sw, ws, records=rec)
         if ev is not None:
             ev[1].record(stream)
-        r.splat_forward(rec, ws)
+        r.splat_forward(rec, op, ws)
         if ev is not None:
             ev[2].record(stream)
-        _, kept, nk, _, _ = r.blend(rec, op, desc, ws, store_lists=store, pyramid=pyr)
+        _, kept, nk, _, _ = r.blend(N, desc, ws, store_lists=store, pyramid=pyr)
         if ev is not None:
             ev[3].record(stream)
         r.splat_backward(rec, op, desc, G, ws, kept if store else None, nk if store else None, grads=grads)
@@ -289,7 +289,7 @@ def run_ours(args):
                 for q, name in enumerate(["project", "splat", "blend", "backward"])}
 
     # counters of the frame (untimed)
-    _, kept, nk, tfin, nfrag = r.blend(rec, op, desc, ws, stats=True)
+    _, kept, nk, tfin, nfrag = r.blend(N, desc, ws, stats=True)
     V = int((rec[:, 2] > 0).sum().item())
     F = int(nfrag.to(torch.int64).sum().item())
     Fk = int(nk.to(torch.int64).sum().item())
@@ -358,8 +358,8 @@ def run_ours(args):
     f0.record(stream)
     for _ in range(args.steps):
         r.project(pos, sw, ws, records=rec)
-        r.splat_forward(rec, ws)
-        r.blend(rec, op, desc, ws, pyramid=pyr)
+        r.splat_forward(rec, op, ws)
+        r.blend(N, desc, ws, pyramid=pyr)
     f1.record(stream)
     torch.cuda.synchronize(dev)
     fwd_ms = max_over_ranks(f0.elapsed_time(f1), world, dev) / args.steps

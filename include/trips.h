@@ -74,7 +74,7 @@
  *   number of candidate fragments of the pixel before the K cap.
  *
  * Sizes: n < 2^27 points, 1 <= n_layers <= 16, K in {4, 8, 16, 32},
- * 1 <= D <= 64, width and height in [1, 32768].
+ * 1 <= D <= 64, width and height in [1, 32768], tile_w * tile_h <= 1024.
  */
 #ifndef TRIPS_H
 #define TRIPS_H
@@ -164,28 +164,32 @@ TP_API tp_status tp_project(const tp_config *cfg, const tp_camera *cam, int64_t 
 
 /*
  * Offset scan and splatting stages (Sec. 3.6): exclusive scan of the tile
- * counts, then every point writes its record and index into the list of
- * each screen tile its 2x2x2 splat touches.  Needs tp_project of the same
- * frame first.  If the lists exceed the workspace's entry capacity,
- * TP_FLAG_CAPACITY is set and the frame's outputs are not valid.
+ * counts, then every point writes its fragment key (z, i) and its payload
+ * (x, y, s, alpha) into the list of each screen tile its 2x2x2 splat
+ * touches (24 bytes per entry, in the workspace).  Needs tp_project of the
+ * same frame first.
+ *   records [n][4] (device, read; from tp_project), opacity [n] (device, read)
+ * If the lists exceed the workspace's entry capacity, TP_FLAG_CAPACITY is set
+ * and the frame's outputs are not valid.
  */
-TP_API tp_status tp_splat_forward(const tp_config *cfg, const tp_camera *cam, int64_t n, const float *records, void *ws,
-                           int64_t ws_bytes, tp_stream_t stream);
+TP_API tp_status tp_splat_forward(const tp_config *cfg, const tp_camera *cam, int64_t n, const float *records,
+                                  const float *opacity, void *ws, int64_t ws_bytes, tp_stream_t stream);
 
 /*
  * Sort-and-accumulate stage (Sec. 3.2 Eq. 6-7, Sec. 3.6): for every pyramid
  * pixel, the K smallest (z, index) fragments in order, blended front to back:
  *   C = sum_m T_m gamma_m tau_m,  T_m = prod_{i<m} (1 - gamma_i),
  *   gamma = beta iota alpha (Eq. 3).
- *   records [n][4], opacity [n], desc [n][D] (device, read)
+ * The fragments come from the workspace's tile lists (tp_splat_forward).
+ *   desc [n][D] (device, read)
  *   pyramid [P][D] (device, written; every pixel)
  *   kept [P][K], n_kept [P], t_final [P], n_frag [P] (device, written;
  *   each may be NULL).  kept and n_kept are what tp_splat_backward reads in
  *   TP_STORE_LISTS mode.
  */
-TP_API tp_status tp_blend(const tp_config *cfg, const tp_camera *cam, int64_t n, const float *records, const float *opacity,
-                   const void *desc, float *pyramid, uint32_t *kept, uint8_t *n_kept, float *t_final,
-                   uint32_t *n_frag, void *ws, int64_t ws_bytes, tp_stream_t stream);
+TP_API tp_status tp_blend(const tp_config *cfg, const tp_camera *cam, int64_t n, const void *desc, float *pyramid,
+                          uint32_t *kept, uint8_t *n_kept, float *t_final, uint32_t *n_frag, void *ws,
+                          int64_t ws_bytes, tp_stream_t stream);
 
 /*
  * Backward pass (Sec. 3.6 "for the backwards pass, the sorted per-pixel lists

@@ -50,10 +50,10 @@ _SIGS = {
     "tp_workspace_bytes": (_I64, [ctypes.POINTER(tp_config), ctypes.POINTER(tp_camera), _I64, _I64]),
     "tp_project": (ctypes.c_int, [ctypes.POINTER(tp_config), ctypes.POINTER(tp_camera), _I64, _P, _P, _P, _P, _I64,
                                   _P]),
-    "tp_splat_forward": (ctypes.c_int, [ctypes.POINTER(tp_config), ctypes.POINTER(tp_camera), _I64, _P, _P, _I64,
-                                        _P]),
+    "tp_splat_forward": (ctypes.c_int, [ctypes.POINTER(tp_config), ctypes.POINTER(tp_camera), _I64, _P, _P, _P,
+                                        _I64, _P]),
     "tp_blend": (ctypes.c_int, [ctypes.POINTER(tp_config), ctypes.POINTER(tp_camera), _I64, _P, _P, _P, _P, _P, _P,
-                                _P, _P, _P, _I64, _P]),
+                                _P, _I64, _P]),
     "tp_splat_backward": (ctypes.c_int, [ctypes.POINTER(tp_config), ctypes.POINTER(tp_camera), _I64, _P, _P, _P, _P,
                                          _P, _P, _P, _P, _P, _P, _P, _I64, _P]),
     "tp_get_status": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int32)]),

@@ -57,8 +57,7 @@ tp_status make_frame(const tp_config *cfg, const tp_camera *cam, Frame &F)
     const int tw = cfg->tile_w > 0 ? cfg->tile_w : 16;
     const int th = cfg->tile_h > 0 ? cfg->tile_h : 16;
     if (tw > 64 || th > 64 || cfg->tile_w < 0 || cfg->tile_h < 0) return TP_ERR_INVALID_ARG;
-    const size_t smem = (size_t)tw * th * ((size_t)cfg->K * 8 + 4);
-    if (smem > kMaxTileSmem) return TP_ERR_UNSUPPORTED;
+    if (tw * th > 1024) return TP_ERR_UNSUPPORTED;  // one thread per tile pixel
     std::memset(&F, 0, sizeof(F));
     F.fx = cam->fx; F.fy = cam->fy; F.cx = cam->cx; F.cy = cam->cy;
     std::memcpy(F.R, cam->R, sizeof(F.R));
@@ -82,11 +81,27 @@ tp_status make_frame(const tp_config *cfg, const tp_camera *cam, Frame &F)
     }
     F.tile_base[F.n_layers] = tiles;
     F.n_tiles = tiles;
+    // Tile CTAs: one thread per pixel; the chunk of tile-list entries merged at
+    // a time is sized so that a CTA's shared memory stays near 72 KB (three
+    // CTAs per SM) when the kept lists leave room for it.
+    F.tile_px = tw * th;
+    F.tile_threads = (F.tile_px + 31) / 32 * 32;
+    const int64_t kept_bytes = (int64_t)F.tile_px * F.K * 12;
+    const int64_t avail = 72 * 1024 - kept_bytes - (3 * F.tile_threads + 32) * 4;
+    int64_t chunk = avail / 48;
+    if (chunk < 128) chunk = 128;
+    if (chunk > 2048) chunk = 2048;
+    F.chunk = (int)chunk;
+    if (tpk::tile_smem_bytes(F, true) > kMaxTileSmem) return TP_ERR_UNSUPPORTED;
     return TP_OK;
 }
 
+// Workspace: status word, tile counts, tile offsets, fill cursors, then the
+// tile lists as two arrays: 8-byte fragment keys and 16-byte payloads.
+constexpr int64_t kEntryBytes = 24;
+
 struct WsLayout {
-    int64_t count, off, cursor, idx, rec, end;
+    int64_t count, off, cursor, key, pay, end;
 };
 
 WsLayout layout_for(const Frame &F, int64_t capacity)
@@ -96,9 +111,9 @@ WsLayout layout_for(const Frame &F, int64_t capacity)
     w.count = kAlign;
     w.off = align_up(w.count + 4 * T);
     w.cursor = align_up(w.off + 4 * (T + 1));
-    w.idx = align_up(w.cursor + 4 * T);
-    w.rec = align_up(w.idx + 4 * capacity);
-    w.end = w.rec + 16 * capacity;
+    w.key = align_up(w.cursor + 4 * T);
+    w.pay = align_up(w.key + 8 * capacity);
+    w.end = w.pay + 16 * capacity;
     return w;
 }
 
@@ -107,9 +122,9 @@ int64_t capacity_for(const Frame &F, int64_t ws_bytes)
 {
     const WsLayout w0 = layout_for(F, 0);
     if (ws_bytes < w0.end) return -1;
-    // align_up only adds bytes, so (ws_bytes - idx) / 20 is an upper bound;
-    // alignment costs < 256 bytes, so the loop runs at most ~13 times.
-    int64_t c = (ws_bytes - w0.idx) / 20;
+    // align_up only adds bytes, so (ws_bytes - key) / 24 is an upper bound;
+    // alignment costs < 256 bytes, so the loop runs at most ~11 times.
+    int64_t c = (ws_bytes - w0.key) / kEntryBytes;
     if (c < 0) c = 0;
     while (c > 0 && layout_for(F, c).end > ws_bytes) --c;
     if (c > 0x7FFFFFFF) c = 0x7FFFFFFF;
@@ -127,8 +142,8 @@ tp_status bind_workspace(const Frame &F, void *ws, int64_t ws_bytes, Workspace &
     W.tile_count = reinterpret_cast<unsigned *>(base + w.count);
     W.tile_off = reinterpret_cast<unsigned *>(base + w.off);
     W.tile_cursor = reinterpret_cast<unsigned *>(base + w.cursor);
-    W.bucket_idx = reinterpret_cast<unsigned *>(base + w.idx);
-    W.bucket_rec = reinterpret_cast<float4 *>(base + w.rec);
+    W.bucket_key = reinterpret_cast<unsigned long long *>(base + w.key);
+    W.bucket_pay = reinterpret_cast<float4 *>(base + w.pay);
     W.capacity = (unsigned)cap;
     return TP_OK;
 }
@@ -145,6 +160,14 @@ tp_status common_checks(const tp_config *cfg, const tp_camera *cam, int64_t n, v
 tp_status from_cuda(cudaError_t e) { return e == cudaSuccess ? TP_OK : TP_ERR_CUDA; }
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Descriptors can be read four channels at a time when D is a multiple of 4
+// and the rows stay aligned to four elements.
+int desc_vector_ok(const tp_config *cfg, const void *desc)
+{
+    const uintptr_t elem = cfg->desc_dtype == TP_BF16 ? 2 : 4;
+    return (cfg->desc_dim % 4) == 0 && ((uintptr_t)desc % (4 * elem)) == 0;
+}
 
 }  // namespace
 
@@ -184,30 +207,30 @@ tp_status tp_project(const tp_config *cfg, const tp_camera *cam, int64_t n, cons
                                                (cudaStream_t)stream));
 }
 
-tp_status tp_splat_forward(const tp_config *cfg, const tp_camera *cam, int64_t n, const float *records, void *ws,
-                           int64_t ws_bytes, tp_stream_t stream)
+tp_status tp_splat_forward(const tp_config *cfg, const tp_camera *cam, int64_t n, const float *records,
+                           const float *opacity, void *ws, int64_t ws_bytes, tp_stream_t stream)
 {
     Frame F;
     Workspace W;
     tp_status s = common_checks(cfg, cam, n, ws, ws_bytes, F, W);
     if (s != TP_OK) return s;
-    if (n > 0 && (!records || !aligned16(records))) return TP_ERR_INVALID_ARG;
-    return from_cuda(
-        tpk::launch_scan_fill(F, W, n, reinterpret_cast<const float4 *>(records), (cudaStream_t)stream));
+    if (n > 0 && (!records || !opacity || !aligned16(records))) return TP_ERR_INVALID_ARG;
+    return from_cuda(tpk::launch_scan_fill(F, W, n, reinterpret_cast<const float4 *>(records), opacity,
+                                           (cudaStream_t)stream));
 }
 
-tp_status tp_blend(const tp_config *cfg, const tp_camera *cam, int64_t n, const float *records, const float *opacity,
-                   const void *desc, float *pyramid, uint32_t *kept, uint8_t *n_kept, float *t_final,
-                   uint32_t *n_frag, void *ws, int64_t ws_bytes, tp_stream_t stream)
+tp_status tp_blend(const tp_config *cfg, const tp_camera *cam, int64_t n, const void *desc, float *pyramid,
+                   uint32_t *kept, uint8_t *n_kept, float *t_final, uint32_t *n_frag, void *ws, int64_t ws_bytes,
+                   tp_stream_t stream)
 {
     Frame F;
     Workspace W;
     tp_status s = common_checks(cfg, cam, n, ws, ws_bytes, F, W);
     if (s != TP_OK) return s;
     if (!pyramid) return TP_ERR_INVALID_ARG;
-    if (n > 0 && (!records || !opacity || !desc || !aligned16(records))) return TP_ERR_INVALID_ARG;
-    return from_cuda(tpk::launch_blend(F, W, reinterpret_cast<const float4 *>(records), opacity, desc,
-                                       cfg->desc_dtype, pyramid, kept, n_kept, t_final, n_frag,
+    if (n > 0 && !desc) return TP_ERR_INVALID_ARG;
+    F.desc_vec = desc_vector_ok(cfg, desc) && aligned16(pyramid);
+    return from_cuda(tpk::launch_blend(F, W, desc, cfg->desc_dtype, pyramid, kept, n_kept, t_final, n_frag,
                                        (cudaStream_t)stream));
 }
 
@@ -225,6 +248,7 @@ tp_status tp_splat_backward(const tp_config *cfg, const tp_camera *cam, int64_t 
     if (n > 0 && (!records || !opacity || !desc || !grad_pos || !grad_size_w || !grad_opacity || !grad_desc ||
                   !aligned16(records)))
         return TP_ERR_INVALID_ARG;
+    F.desc_vec = desc_vector_ok(cfg, desc);
     return from_cuda(tpk::launch_backward(F, W, n, reinterpret_cast<const float4 *>(records), opacity, desc,
                                           cfg->desc_dtype, kept, n_kept, grad_pyramid, grad_pos, grad_size_w,
                                           grad_opacity, grad_desc, (cudaStream_t)stream));

@@ -98,18 +98,22 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Frame F, Workspace W)
     }
 }
 
-// Splat: every point appends its record and index to each tile it touches.
-__global__ void __launch_bounds__(kBlock) k_fill(Frame F, Workspace W, long long n, const float4 *__restrict__ rec)
+// Splat: every point appends its fragment key (z, i) and its blend payload
+// (x, y, s, alpha) to the list of each tile it touches.
+__global__ void __launch_bounds__(kBlock) k_fill(Frame F, Workspace W, long long n, const float4 *__restrict__ rec,
+                                                 const float *__restrict__ opacity)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const float4 r = rec[i];
         if (!(r.z > 0.0f)) continue;  // culled
+        const unsigned long long key = frag_key(r.z, (unsigned)i);
+        const float4 pay = make_float4(r.x, r.y, r.w, __ldg(opacity + i));
         for_each_tile(F, r, [&](int t) {
             const unsigned e = W.tile_off[t] + atomicAdd(W.tile_cursor + t, 1u);
             if (e < W.capacity) {
-                W.bucket_rec[e] = r;
-                W.bucket_idx[e] = (unsigned)i;
+                W.bucket_key[e] = key;
+                W.bucket_pay[e] = pay;
             }
         });
     }
@@ -136,12 +140,12 @@ cudaError_t launch_project_count(const Frame &F, const Workspace &W, long long n
 }
 
 cudaError_t launch_scan_fill(const Frame &F, const Workspace &W, long long n, const float4 *rec,
-                             cudaStream_t stream)
+                             const float *opacity, cudaStream_t stream)
 {
     k_scan_tiles<<<1, 1024, 0, stream>>>(F, W);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || n == 0) return e;
-    k_fill<<<grid_for(n), kBlock, 0, stream>>>(F, W, n, rec);
+    k_fill<<<grid_for(n), kBlock, 0, stream>>>(F, W, n, rec, opacity);
     return cudaGetLastError();
 }
 

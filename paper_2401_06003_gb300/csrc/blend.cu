@@ -1,16 +1,20 @@
 // blend.cu -- combined sort and accumulate stage and its adjoint (TRIPS Sec. 3.2, 3.6).
 //
-// One CTA owns one screen tile of one pyramid layer.  It streams the tile's
-// (point, tile) entries written by the splat pass, computes each point's
-// taps inside the tile (Eq. 3-5) and inserts the fragment key (z, i) into a
-// per-pixel sorted buffer of K slots in shared memory.  The insertion is a
-// cascade of atomicMin on 64-bit keys: each slot keeps the smaller of its
-// value and the incoming key and passes the larger one on.  Whatever the
-// interleaving, slot m ends with the m-th smallest key of all fragments of
-// the pixel, so the buffer holds exactly the K front-most fragments in
-// (depth, index) order -- the list the paper sorts per pixel and clamps to
-// 16 elements (Sec. 3.2), without materialising the full list.  The pixel
-// then blends its kept fragments front to back (Eq. 6-7) in registers.
+// One CTA owns one screen tile of one pyramid layer, one thread per pixel.
+// It reads the tile's list of (point, tile) entries written by the splat
+// pass in chunks.  For each chunk it
+//   1. counts the chunk's fragments per pixel (the point's taps inside the
+//      tile, Eq. 3-5),
+//   2. turns the counts into offsets with a block scan,
+//   3. scatters the chunk's fragment keys (z, i) into per-pixel runs in
+//      shared memory,
+//   4. lets each thread merge its own pixel's run into that pixel's sorted
+//      list of the K smallest keys (a private insertion sort, no atomics).
+// After the last chunk every pixel holds exactly the K front-most fragments
+// of its full list in (depth, index) order -- the list the paper sorts per
+// pixel and clamps to 16 elements (Sec. 3.2) -- without ever storing the full
+// list, and the cost of a tile is linear in its fragments whatever their
+// arrival order.  The pixel then blends its list front to back (Eq. 6-7).
 //
 // The backward kernels run the adjoint of the blend per pixel back to front
 // over the kept list (division-free recurrence) and scatter the point
@@ -18,36 +22,6 @@
 #include "common.cuh"
 
 namespace tpk {
-
-__device__ __forceinline__ unsigned long long ld_relaxed_shared(const unsigned long long *p)
-{
-    unsigned long long v;
-    asm volatile("ld.relaxed.cta.shared.b64 %0, [%1];"
-                 : "=l"(v)
-                 : "r"((unsigned)__cvta_generic_to_shared(p))
-                 : "memory");
-    return v;
-}
-
-// Insert a key into a pixel's K sorted slots.  Slots only ever decrease, and
-// at every instant they are sorted; a slot that is already smaller than the
-// key stays smaller, so the search may skip it.
-template <int K>
-__device__ __forceinline__ void kbuf_insert(unsigned long long *slots, unsigned long long key)
-{
-    if (key >= ld_relaxed_shared(slots + K - 1)) return;
-    int lo = 0, hi = K - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (ld_relaxed_shared(slots + mid) > key) hi = mid;
-        else lo = mid + 1;
-    }
-    for (int j = lo; j < K; ++j) {
-        const unsigned long long old = atomicMin(slots + j, key);
-        if (old == kEmptyKey) return;
-        key = old > key ? old : key;
-    }
-}
 
 struct TileGeom {
     int L, x0, y0;
@@ -63,221 +37,346 @@ __device__ __forceinline__ TileGeom tile_geom(const Frame &F, int tile)
     return g;
 }
 
-// Build the K-slot buffers and candidate counts of every pixel of the tile.
-template <int K>
-__device__ void build_kbuffer(const Frame &F, const Workspace &W, int tile, const TileGeom &g,
-                              unsigned long long *kb, unsigned *nf)
+// Shared-memory layout of a tile CTA (offsets in bytes, all 16-aligned).
+struct TileSmem {
+    unsigned long long *tk_key;  // [K][tile_px]  sorted kept keys, slot-major
+    unsigned *tk_e;              // [K][tile_px]  workspace entry of each kept key
+    unsigned long long *ck;      // [4 chunk]     chunk fragment keys, grouped by pixel
+    unsigned *ce;                // [4 chunk]     chunk fragment entries
+    float *scratch;              // aliases ck/ce after the last chunk
+    unsigned *cnt, *off, *cur;   // [tile_threads]
+    unsigned *wsum;              // [32]
+};
+
+__host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
+
+__host__ __device__ inline size_t chunk_area_bytes(const Frame &F, bool backward)
 {
-    const int TW = F.tile_w, TH = F.tile_h, TP = TW * TH;
-    for (int q = threadIdx.x; q < TP * K; q += blockDim.x) kb[q] = kEmptyKey;
-    for (int q = threadIdx.x; q < TP; q += blockDim.x) nf[q] = 0u;
+    size_t a = (size_t)4 * F.chunk * (sizeof(unsigned long long) + sizeof(unsigned));
+    // scratch after the chunks: the blend keeps T_m gamma_m, the adjoint gamma_m and T_m
+    const size_t s = (size_t)(backward ? 2 : 1) * F.K * F.tile_px * sizeof(float);
+    return align16(a > s ? a : s);
+}
+
+__device__ __forceinline__ TileSmem carve(const Frame &F, unsigned char *base, bool backward)
+{
+    TileSmem m;
+    const size_t TP = F.tile_px, NT = F.tile_threads;
+    size_t o = 0;
+    m.tk_key = reinterpret_cast<unsigned long long *>(base + o);
+    o += align16(TP * F.K * sizeof(unsigned long long));
+    m.tk_e = reinterpret_cast<unsigned *>(base + o);
+    o += align16(TP * F.K * sizeof(unsigned));
+    m.ck = reinterpret_cast<unsigned long long *>(base + o);
+    m.ce = reinterpret_cast<unsigned *>(base + o + (size_t)4 * F.chunk * sizeof(unsigned long long));
+    m.scratch = reinterpret_cast<float *>(base + o);
+    o += chunk_area_bytes(F, backward);
+    m.cnt = reinterpret_cast<unsigned *>(base + o);
+    m.off = m.cnt + NT;
+    m.cur = m.off + NT;
+    m.wsum = m.cur + NT;
+    return m;
+}
+
+size_t tile_smem_bytes(const Frame &F, bool backward)
+{
+    const size_t TP = F.tile_px, NT = F.tile_threads;
+    return align16(TP * F.K * sizeof(unsigned long long)) + align16(TP * F.K * sizeof(unsigned)) +
+           chunk_area_bytes(F, backward) + (3 * NT + 32) * sizeof(unsigned);
+}
+
+// Exclusive scan of v over the CTA (blockDim.x <= 1024, a multiple of 32).
+__device__ __forceinline__ unsigned block_exclusive_scan(unsigned v, unsigned *wsum)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
     __syncthreads();
+    if (warp == 0) {
+        unsigned w = lane < nw ? wsum[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    return x - v + (warp > 0 ? wsum[warp - 1] : 0u);
+}
+
+// The taps of workspace entry e that fall inside the tile; calls fn(px) per tap.
+template <class Fn>
+__device__ __forceinline__ void entry_taps(const Frame &F, const TileGeom &g, const float4 &pay, Fn &&fn)
+{
+    const int L = g.L;
+    float iota, diota;
+    if (!layer_weight(pay.z, L, F.n_layers, F.eps, iota, diota)) return;
+    const AxisTaps ax = axis_taps(pay.x, L, F.lw[L]);
+    const AxisTaps ay = axis_taps(pay.y, L, F.lh[L]);
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        if (!(b ? ay.t1 : ay.t0)) continue;
+        const int k = ay.j0 + b - g.y0;
+        if (k < 0 || k >= F.tile_h) continue;
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            if (!(a ? ax.t1 : ax.t0)) continue;
+            const int j = ax.j0 + a - g.x0;
+            if (j < 0 || j >= F.tile_w) continue;
+            fn(k * F.tile_w + j);
+        }
+    }
+}
+
+// Insert (key, e) into this thread's sorted list of at most K keys.
+template <int K>
+__device__ __forceinline__ void topk_insert(unsigned long long *kk, unsigned *ke, int TP, int px, int &n_top,
+                                            unsigned long long key, unsigned e)
+{
+    int pos;
+    if (n_top == K) {
+        if (key >= kk[(K - 1) * TP + px]) return;
+        pos = K - 1;
+    } else {
+        pos = n_top++;
+    }
+    while (pos > 0) {
+        const unsigned long long prev = kk[(pos - 1) * TP + px];
+        if (prev < key) break;
+        kk[pos * TP + px] = prev;
+        ke[pos * TP + px] = ke[(pos - 1) * TP + px];
+        --pos;
+    }
+    kk[pos * TP + px] = key;
+    ke[pos * TP + px] = e;
+}
+
+// Builds every pixel's kept list.  Thread t owns pixel t (t < tile_px).
+// Returns the kept count of the thread's pixel; *nfrag gets its candidates.
+template <int K>
+__device__ int build_topk(const Frame &F, const Workspace &W, int tile, const TileGeom &g, const TileSmem &S,
+                          unsigned *nfrag)
+{
+    const int TP = F.tile_px, tid = threadIdx.x, NT = blockDim.x;
+    const bool owner = tid < TP;
+    S.cnt[tid] = 0u;
+    S.cur[tid] = 0u;
     unsigned end = W.tile_off[tile + 1];
     if (end > W.capacity) end = W.capacity;
     unsigned beg = W.tile_off[tile];
     if (beg > end) beg = end;
-    const int L = g.L;
-    for (unsigned e = beg + threadIdx.x; e < end; e += blockDim.x) {
-        const float4 r = W.bucket_rec[e];
-        const unsigned i = W.bucket_idx[e];
-        float iota, diota;
-        if (!layer_weight(r.w, L, F.n_layers, F.eps, iota, diota)) continue;
-        const AxisTaps ax = axis_taps(r.x, L, F.lw[L]);
-        const AxisTaps ay = axis_taps(r.y, L, F.lh[L]);
-        const unsigned long long key = frag_key(r.z, i);
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            if (!(b ? ay.t1 : ay.t0)) continue;
-            const int k = ay.j0 + b - g.y0;
-            if (k < 0 || k >= TH) continue;
-#pragma unroll
-            for (int a = 0; a < 2; ++a) {
-                if (!(a ? ax.t1 : ax.t0)) continue;
-                const int j = ax.j0 + a - g.x0;
-                if (j < 0 || j >= TW) continue;
-                const int px = k * TW + j;
-                atomicAdd(nf + px, 1u);
-                kbuf_insert<K>(kb + px * K, key);
-            }
-        }
-    }
+    int n_top = 0;
+    unsigned nfr = 0;
     __syncthreads();
+    for (unsigned c0 = beg; c0 < end; c0 += (unsigned)F.chunk) {
+        const unsigned c1 = min(end, c0 + (unsigned)F.chunk);
+        for (unsigned e = c0 + tid; e < c1; e += NT)
+            entry_taps(F, g, W.bucket_pay[e], [&](int px) { atomicAdd(S.cnt + px, 1u); });
+        __syncthreads();
+        const unsigned my = S.cnt[tid];
+        S.off[tid] = block_exclusive_scan(my, S.wsum);
+        __syncthreads();
+        for (unsigned e = c0 + tid; e < c1; e += NT) {
+            const unsigned long long key = W.bucket_key[e];
+            entry_taps(F, g, W.bucket_pay[e], [&](int px) {
+                const unsigned q = S.off[px] + atomicAdd(S.cur + px, 1u);
+                S.ck[q] = key;
+                S.ce[q] = e;
+            });
+        }
+        __syncthreads();
+        if (owner) {
+            const unsigned a = S.off[tid];
+            for (unsigned q = a; q < a + my; ++q) topk_insert<K>(S.tk_key, S.tk_e, TP, tid, n_top, S.ck[q], S.ce[q]);
+            nfr += my;
+        }
+        S.cnt[tid] = 0u;
+        S.cur[tid] = 0u;
+        __syncthreads();
+    }
+    *nfrag = nfr;
+    return n_top;
 }
 
-// Tap weight beta * iota of point record r at layer-L pixel (j, k), with the
-// pieces the adjoint needs.
+// beta * iota of a point with payload (x, y, s, alpha) at layer-L pixel (j, k),
+// with the pieces the adjoint needs.
 struct FragW {
     float wx, wy, dwx, dwy, iota, diota;
 };
 
-__device__ __forceinline__ FragW frag_weights(const Frame &F, const float4 &r, int L, int j, int k)
+__device__ __forceinline__ FragW frag_weights(const Frame &F, float x, float y, float s, int L, int j, int k)
 {
     FragW w;
-    layer_weight(r.w, L, F.n_layers, F.eps, w.iota, w.diota);
-    const AxisTaps ax = axis_taps(r.x, L, F.lw[L]);
-    const AxisTaps ay = axis_taps(r.y, L, F.lh[L]);
+    layer_weight(s, L, F.n_layers, F.eps, w.iota, w.diota);
+    const AxisTaps ax = axis_taps(x, L, F.lw[L]);
+    const AxisTaps ay = axis_taps(y, L, F.lh[L]);
     tap_weight(ax, j, L, w.wx, w.dwx);
     tap_weight(ay, k, L, w.wy, w.dwy);
     return w;
 }
 
-// Blend one pixel's kept fragments (ids[0..nk)) and write its outputs.
-template <int K, typename DescT>
-__device__ __forceinline__ void blend_pixel(const Frame &F, int L, int j, int k, long long pix, const unsigned *ids,
-                                            int nk, unsigned nfrag, const float4 *__restrict__ rec,
-                                            const float *__restrict__ opacity, const DescT *__restrict__ desc,
-                                            float *__restrict__ pyramid, unsigned *__restrict__ kept,
-                                            unsigned char *__restrict__ n_kept, float *__restrict__ t_final,
-                                            unsigned *__restrict__ n_frag)
+// Four channels [d0, d0 + 4) of descriptor i (zeros past D).
+template <typename DescT>
+__device__ __forceinline__ float4 load_desc4(const DescT *__restrict__ desc, unsigned i, int D, int d0, int vec)
 {
-    float wgt[K];
-    float T = 1.0f;
-#pragma unroll
-    for (int m = 0; m < K; ++m) {
-        wgt[m] = 0.0f;
-        if (m < nk) {
-            const unsigned i = ids[m];
-            const float4 r = rec[i];
-            const FragW w = frag_weights(F, r, L, j, k);
-            const float g = w.wx * w.wy * w.iota * __ldg(opacity + i);
-            wgt[m] = T * g;
-            T = T * (1.0f - g);
+    const DescT *p = desc + (long long)i * D + d0;
+    if (vec) {
+        if constexpr (sizeof(DescT) == 4) {
+            return __ldg(reinterpret_cast<const float4 *>(p));
+        } else {
+            const uint2 raw = __ldg(reinterpret_cast<const uint2 *>(p));
+            const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162 *>(&raw.x);
+            const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162 *>(&raw.y);
+            const float2 a = __bfloat1622float2(lo), b = __bfloat1622float2(hi);
+            return make_float4(a.x, a.y, b.x, b.y);
         }
     }
-    const int D = F.D;
-    float *out = pyramid + pix * D;
-    for (int d = 0; d < D; ++d) {
-        float c = 0.0f;
+    float v[4];
 #pragma unroll
-        for (int m = 0; m < K; ++m)
-            if (m < nk) c += wgt[m] * load_desc(desc + (long long)ids[m] * D + d);
-        out[d] = c;
+    for (int c = 0; c < 4; ++c) v[c] = d0 + c < D ? load_desc(p + c) : 0.0f;
+    return make_float4(v[0], v[1], v[2], v[3]);
+}
+
+template <int K, typename DescT>
+__global__ void k_tile_blend(Frame F, Workspace W, const DescT *__restrict__ desc, float *__restrict__ pyramid,
+                             unsigned *__restrict__ kept, unsigned char *__restrict__ n_kept,
+                             float *__restrict__ t_final, unsigned *__restrict__ n_frag)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const TileSmem S = carve(F, smem_raw, false);
+    const int tile = blockIdx.x;
+    const TileGeom g = tile_geom(F, tile);
+    unsigned nfr;
+    const int nk = build_topk<K>(F, W, tile, g, S, &nfr);
+    const int TP = F.tile_px, tid = threadIdx.x, L = g.L;
+    if (tid >= TP) return;
+    const int j = g.x0 + tid % F.tile_w, k = g.y0 + tid / F.tile_w;
+    if (j >= F.lw[L] || k >= F.lh[L]) return;
+    const long long pix = F.pix_base[L] + (long long)k * F.lw[L] + j;
+    // front to back: weights T_m gamma_m (Eq. 6-7)
+    float T = 1.0f;
+    for (int m = 0; m < nk; ++m) {
+        const float4 pay = W.bucket_pay[S.tk_e[m * TP + tid]];
+        const FragW w = frag_weights(F, pay.x, pay.y, pay.z, L, j, k);
+        const float gam = w.wx * w.wy * w.iota * pay.w;
+        S.scratch[m * TP + tid] = T * gam;
+        T = T * (1.0f - gam);
+    }
+    const int D = F.D;
+    for (int d0 = 0; d0 < D; d0 += 4) {
+        float4 c = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        for (int m = 0; m < nk; ++m) {
+            const unsigned i = (unsigned)(S.tk_key[m * TP + tid] & 0xFFFFFFFFull);
+            const float wgt = S.scratch[m * TP + tid];
+            const float4 t = load_desc4(desc, i, D, d0, F.desc_vec);
+            c.x += wgt * t.x;
+            c.y += wgt * t.y;
+            c.z += wgt * t.z;
+            c.w += wgt * t.w;
+        }
+        float *out = pyramid + pix * D + d0;
+        if (F.desc_vec) {
+            *reinterpret_cast<float4 *>(out) = c;
+        } else {
+            const float cv[4] = {c.x, c.y, c.z, c.w};
+            for (int q = 0; q < 4 && d0 + q < D; ++q) out[q] = cv[q];
+        }
     }
     if (kept) {
-#pragma unroll
-        for (int m = 0; m < K; ++m) kept[pix * K + m] = m < nk ? ids[m] : kNoPoint;
+        for (int m = 0; m < K; ++m)
+            kept[pix * K + m] = m < nk ? (unsigned)(S.tk_key[m * TP + tid] & 0xFFFFFFFFull) : kNoPoint;
     }
     if (n_kept) n_kept[pix] = (unsigned char)nk;
     if (t_final) t_final[pix] = T;
-    if (n_frag) n_frag[pix] = nfrag;
+    if (n_frag) n_frag[pix] = nfr;
 }
 
-template <int K, typename DescT>
-__global__ void __launch_bounds__(kBlock) k_tile_blend(Frame F, Workspace W, const float4 *__restrict__ rec,
-                                                       const float *__restrict__ opacity,
-                                                       const DescT *__restrict__ desc, float *__restrict__ pyramid,
-                                                       unsigned *__restrict__ kept, unsigned char *__restrict__ n_kept,
-                                                       float *__restrict__ t_final, unsigned *__restrict__ n_frag)
-{
-    extern __shared__ unsigned long long smem[];
-    const int TW = F.tile_w, TP = F.tile_w * F.tile_h;
-    unsigned long long *kb = smem;
-    unsigned *nf = reinterpret_cast<unsigned *>(smem + TP * K);
-    const int tile = blockIdx.x;
-    const TileGeom g = tile_geom(F, tile);
-    build_kbuffer<K>(F, W, tile, g, kb, nf);
-    const int L = g.L;
-    for (int px = threadIdx.x; px < TP; px += blockDim.x) {
-        const int j = g.x0 + px % TW, k = g.y0 + px / TW;
-        if (j >= F.lw[L] || k >= F.lh[L]) continue;
-        const long long pix = F.pix_base[L] + (long long)k * F.lw[L] + j;
-        const unsigned nfr = nf[px];
-        const int nk = nfr < (unsigned)K ? (int)nfr : K;
-        unsigned ids[K];
-#pragma unroll
-        for (int m = 0; m < K; ++m) ids[m] = m < nk ? (unsigned)(kb[px * K + m] & 0xFFFFFFFFull) : kNoPoint;
-        blend_pixel<K, DescT>(F, L, j, k, pix, ids, nk, nfr, rec, opacity, desc, pyramid, kept, n_kept, t_final,
-                              n_frag);
-    }
-}
-
-// Adjoint of one pixel's blend, scattered into the point gradients.
-template <int K, typename DescT>
-__device__ __forceinline__ void adjoint_pixel(const Frame &F, int L, int j, int k, long long pix, const unsigned *ids,
-                                              int nk, const float4 *__restrict__ rec,
-                                              const float *__restrict__ opacity, const DescT *__restrict__ desc,
-                                              const float *__restrict__ grad_pyr, float *__restrict__ gpos,
-                                              float *__restrict__ gsw, float *__restrict__ gop,
-                                              float *__restrict__ gdesc)
+// Adjoint of one kept fragment, given its forward quantities; scatters the
+// point gradients.  G is the pixel's dL/dC; R the running back-to-front term.
+template <typename DescT>
+__device__ __forceinline__ void adjoint_fragment(const Frame &F, int L, int j, int k, unsigned i, float x, float y,
+                                                 float z, float s, float al, float gam, float Tm, const float *G,
+                                                 float &R, const DescT *__restrict__ desc, float *__restrict__ gpos,
+                                                 float *__restrict__ gsw, float *__restrict__ gop,
+                                                 float *__restrict__ gdesc)
 {
     const int D = F.D;
-    const float *G = grad_pyr + pix * D;
-    float gam[K], Tm[K];
-    float T = 1.0f;
-#pragma unroll
-    for (int m = 0; m < K; ++m) {
-        gam[m] = 0.0f;
-        Tm[m] = 0.0f;
-        if (m < nk) {
-            const unsigned i = ids[m];
-            const FragW w = frag_weights(F, rec[i], L, j, k);
-            const float g = w.wx * w.wy * w.iota * __ldg(opacity + i);
-            gam[m] = g;
-            Tm[m] = T;
-            T = T * (1.0f - g);
-        }
+    const FragW w = frag_weights(F, x, y, s, L, j, k);
+    float gdot = 0.0f;
+    for (int d0 = 0; d0 < D; d0 += 4) {
+        const float4 t = load_desc4(desc, i, D, d0, F.desc_vec);
+        gdot += G[d0] * t.x;
+        if (d0 + 1 < D) gdot += G[d0 + 1] * t.y;
+        if (d0 + 2 < D) gdot += G[d0 + 2] * t.z;
+        if (d0 + 3 < D) gdot += G[d0 + 3] * t.w;
     }
-    float R = 0.0f;
-#pragma unroll
-    for (int m = K - 1; m >= 0; --m) {
-        if (m >= nk) continue;
-        const unsigned i = ids[m];
-        const float4 r = rec[i];
-        const float al = __ldg(opacity + i);
-        const FragW w = frag_weights(F, r, L, j, k);
-        const DescT *c = desc + (long long)i * D;
-        float gdot = 0.0f;
-        for (int d = 0; d < D; ++d) gdot += __ldg(G + d) * load_desc(c + d);
-        const float dg = Tm[m] * (gdot - R);
-        R = gam[m] * gdot + (1.0f - gam[m]) * R;
-        const float tg = Tm[m] * gam[m];
-        float *gd = gdesc + (long long)i * D;
-        for (int d = 0; d < D; ++d) atomicAdd(gd + d, tg * __ldg(G + d));
-        const float beta = w.wx * w.wy;
-        atomicAdd(gop + i, dg * beta * w.iota);
-        const float dw = dg * al;
-        const float gx = dw * w.wy * w.iota * w.dwx;
-        const float gy = dw * w.wx * w.iota * w.dwy;
-        const float gs = dw * beta * w.diota;
-        const float iz = 1.0f / r.z;
-        const float dXc = gx * F.fx * iz;
-        const float dYc = gy * F.fy * iz;
-        const float dZc = -(gx * (r.x - F.cx) + gy * (r.y - F.cy) + gs * r.w) * iz;
-        atomicAdd(gsw + i, gs * F.fx * iz);
-        atomicAdd(gpos + 3 * (long long)i + 0, F.R[0] * dXc + F.R[3] * dYc + F.R[6] * dZc);
-        atomicAdd(gpos + 3 * (long long)i + 1, F.R[1] * dXc + F.R[4] * dYc + F.R[7] * dZc);
-        atomicAdd(gpos + 3 * (long long)i + 2, F.R[2] * dXc + F.R[5] * dYc + F.R[8] * dZc);
-    }
+    const float dg = Tm * (gdot - R);
+    R = gam * gdot + (1.0f - gam) * R;
+    const float tg = Tm * gam;
+    float *gd = gdesc + (long long)i * D;
+    for (int d = 0; d < D; ++d) atomicAdd(gd + d, tg * G[d]);
+    const float beta = w.wx * w.wy;
+    atomicAdd(gop + i, dg * beta * w.iota);
+    const float dw = dg * al;
+    const float gx = dw * w.wy * w.iota * w.dwx;
+    const float gy = dw * w.wx * w.iota * w.dwy;
+    const float gs = dw * beta * w.diota;
+    const float iz = 1.0f / z;
+    const float dXc = gx * F.fx * iz;
+    const float dYc = gy * F.fy * iz;
+    const float dZc = -(gx * (x - F.cx) + gy * (y - F.cy) + gs * s) * iz;
+    atomicAdd(gsw + i, gs * F.fx * iz);
+    atomicAdd(gpos + 3 * (long long)i + 0, F.R[0] * dXc + F.R[3] * dYc + F.R[6] * dZc);
+    atomicAdd(gpos + 3 * (long long)i + 1, F.R[1] * dXc + F.R[4] * dYc + F.R[7] * dZc);
+    atomicAdd(gpos + 3 * (long long)i + 2, F.R[2] * dXc + F.R[5] * dYc + F.R[8] * dZc);
 }
 
-// Backward with the lists recomputed from the tile entries.
+constexpr int kMaxGradD = 64;
+
+// Backward with the lists rebuilt from the workspace's tile lists.
 template <int K, typename DescT>
-__global__ void __launch_bounds__(kBlock) k_tile_backward(Frame F, Workspace W, const float4 *__restrict__ rec,
-                                                          const float *__restrict__ opacity,
-                                                          const DescT *__restrict__ desc,
-                                                          const float *__restrict__ grad_pyr, float *__restrict__ gpos,
-                                                          float *__restrict__ gsw, float *__restrict__ gop,
-                                                          float *__restrict__ gdesc)
+__global__ void k_tile_backward(Frame F, Workspace W, const DescT *__restrict__ desc,
+                                const float *__restrict__ grad_pyr, float *__restrict__ gpos, float *__restrict__ gsw,
+                                float *__restrict__ gop, float *__restrict__ gdesc)
 {
-    extern __shared__ unsigned long long smem[];
-    const int TW = F.tile_w, TP = F.tile_w * F.tile_h;
-    unsigned long long *kb = smem;
-    unsigned *nf = reinterpret_cast<unsigned *>(smem + TP * K);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const TileSmem S = carve(F, smem_raw, true);
     const int tile = blockIdx.x;
     const TileGeom g = tile_geom(F, tile);
-    build_kbuffer<K>(F, W, tile, g, kb, nf);
-    const int L = g.L;
-    for (int px = threadIdx.x; px < TP; px += blockDim.x) {
-        const int j = g.x0 + px % TW, k = g.y0 + px / TW;
-        if (j >= F.lw[L] || k >= F.lh[L]) continue;
-        const unsigned nfr = nf[px];
-        const int nk = nfr < (unsigned)K ? (int)nfr : K;
-        if (nk == 0) continue;
-        const long long pix = F.pix_base[L] + (long long)k * F.lw[L] + j;
-        unsigned ids[K];
-#pragma unroll
-        for (int m = 0; m < K; ++m) ids[m] = m < nk ? (unsigned)(kb[px * K + m] & 0xFFFFFFFFull) : kNoPoint;
-        adjoint_pixel<K, DescT>(F, L, j, k, pix, ids, nk, rec, opacity, desc, grad_pyr, gpos, gsw, gop, gdesc);
+    unsigned nfr;
+    const int nk = build_topk<K>(F, W, tile, g, S, &nfr);
+    const int TP = F.tile_px, tid = threadIdx.x, L = g.L;
+    if (tid >= TP || nk == 0) return;
+    const int j = g.x0 + tid % F.tile_w, k = g.y0 + tid / F.tile_w;
+    if (j >= F.lw[L] || k >= F.lh[L]) return;
+    const long long pix = F.pix_base[L] + (long long)k * F.lw[L] + j;
+    float *gam = S.scratch;                       // [K][TP]
+    float *Tm = S.scratch + (size_t)K * TP;       // [K][TP]
+    float T = 1.0f;
+    for (int m = 0; m < nk; ++m) {
+        const float4 pay = W.bucket_pay[S.tk_e[m * TP + tid]];
+        const FragW w = frag_weights(F, pay.x, pay.y, pay.z, L, j, k);
+        const float gm = w.wx * w.wy * w.iota * pay.w;
+        gam[m * TP + tid] = gm;
+        Tm[m * TP + tid] = T;
+        T = T * (1.0f - gm);
+    }
+    float G[kMaxGradD];
+    const int D = F.D;
+    for (int d = 0; d < D; ++d) G[d] = __ldg(grad_pyr + pix * D + d);
+    float R = 0.0f;
+    for (int m = nk - 1; m >= 0; --m) {
+        const unsigned long long key = S.tk_key[m * TP + tid];
+        const float4 pay = W.bucket_pay[S.tk_e[m * TP + tid]];
+        adjoint_fragment<DescT>(F, L, j, k, (unsigned)(key & 0xFFFFFFFFull), pay.x, pay.y,
+                                __uint_as_float((unsigned)(key >> 32)), pay.z, pay.w, gam[m * TP + tid],
+                                Tm[m * TP + tid], G, R, desc, gpos, gsw, gop, gdesc);
     }
 }
 
@@ -301,10 +400,31 @@ __global__ void __launch_bounds__(kBlock) k_stored_backward(Frame F, long long P
         while (L + 1 < F.n_layers && pix >= F.pix_base[L + 1]) ++L;
         const long long local = pix - F.pix_base[L];
         const int j = (int)(local % F.lw[L]), k = (int)(local / F.lw[L]);
-        unsigned ids[K];
+        float gam[K], Tm[K];
+        float T = 1.0f;
 #pragma unroll
-        for (int m = 0; m < K; ++m) ids[m] = m < nk ? kept[pix * K + m] : kNoPoint;
-        adjoint_pixel<K, DescT>(F, L, j, k, pix, ids, nk, rec, opacity, desc, grad_pyr, gpos, gsw, gop, gdesc);
+        for (int m = 0; m < K; ++m) {
+            if (m < nk) {
+                const unsigned i = kept[pix * K + m];
+                const float4 r = rec[i];
+                const FragW w = frag_weights(F, r.x, r.y, r.w, L, j, k);
+                gam[m] = w.wx * w.wy * w.iota * __ldg(opacity + i);
+                Tm[m] = T;
+                T = T * (1.0f - gam[m]);
+            }
+        }
+        float G[kMaxGradD];
+        const int D = F.D;
+        for (int d = 0; d < D; ++d) G[d] = __ldg(grad_pyr + pix * D + d);
+        float R = 0.0f;
+#pragma unroll
+        for (int m = K - 1; m >= 0; --m) {
+            if (m >= nk) continue;
+            const unsigned i = kept[pix * K + m];
+            const float4 r = rec[i];
+            adjoint_fragment<DescT>(F, L, j, k, i, r.x, r.y, r.z, r.w, __ldg(opacity + i), gam[m], Tm[m], G, R,
+                                    desc, gpos, gsw, gop, gdesc);
+        }
     }
 }
 
@@ -319,22 +439,15 @@ static cudaError_t allow_smem(KernelT kernel, size_t bytes)
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-static size_t tile_smem(const Frame &F, int K)
-{
-    const size_t TP = (size_t)F.tile_w * F.tile_h;
-    return TP * K * sizeof(unsigned long long) + TP * sizeof(unsigned);
-}
-
 template <int K, typename DescT>
-static cudaError_t blend_impl(const Frame &F, const Workspace &W, const float4 *rec, const float *opacity,
-                              const void *desc, float *pyramid, unsigned *kept, unsigned char *n_kept,
-                              float *t_final, unsigned *n_frag, cudaStream_t stream)
+static cudaError_t blend_impl(const Frame &F, const Workspace &W, const void *desc, float *pyramid, unsigned *kept,
+                              unsigned char *n_kept, float *t_final, unsigned *n_frag, cudaStream_t stream)
 {
-    const size_t smem = tile_smem(F, K);
+    const size_t smem = tile_smem_bytes(F, false);
     cudaError_t e = allow_smem(k_tile_blend<K, DescT>, smem);
     if (e != cudaSuccess) return e;
-    k_tile_blend<K, DescT><<<F.n_tiles, kBlock, smem, stream>>>(
-        F, W, rec, opacity, static_cast<const DescT *>(desc), pyramid, kept, n_kept, t_final, n_frag);
+    k_tile_blend<K, DescT><<<F.n_tiles, F.tile_threads, smem, stream>>>(
+        F, W, static_cast<const DescT *>(desc), pyramid, kept, n_kept, t_final, n_frag);
     return cudaGetLastError();
 }
 
@@ -354,11 +467,11 @@ static cudaError_t backward_impl(const Frame &F, const Workspace &W, const float
                                                                         grad_pyr, gpos, gsw, gop, gdesc);
         return cudaGetLastError();
     }
-    const size_t smem = tile_smem(F, K);
+    const size_t smem = tile_smem_bytes(F, true);
     cudaError_t e = allow_smem(k_tile_backward<K, DescT>, smem);
     if (e != cudaSuccess) return e;
-    k_tile_backward<K, DescT><<<F.n_tiles, kBlock, smem, stream>>>(F, W, rec, opacity, d, grad_pyr, gpos, gsw,
-                                                                   gop, gdesc);
+    k_tile_backward<K, DescT><<<F.n_tiles, F.tile_threads, smem, stream>>>(F, W, d, grad_pyr, gpos, gsw, gop,
+                                                                           gdesc);
     return cudaGetLastError();
 }
 
@@ -371,16 +484,16 @@ static cudaError_t backward_impl(const Frame &F, const Workspace &W, const float
     default: return cudaErrorInvalidValue;                          \
     }
 
-cudaError_t launch_blend(const Frame &F, const Workspace &W, const float4 *rec, const float *opacity,
-                         const void *desc, int desc_dtype, float *pyramid, unsigned *kept, unsigned char *n_kept,
-                         float *t_final, unsigned *n_frag, cudaStream_t stream)
+cudaError_t launch_blend(const Frame &F, const Workspace &W, const void *desc, int desc_dtype, float *pyramid,
+                         unsigned *kept, unsigned char *n_kept, float *t_final, unsigned *n_frag,
+                         cudaStream_t stream)
 {
     if (desc_dtype == TP_BF16) {
-        TPK_DISPATCH_K(F.K, return (blend_impl<KC, __nv_bfloat16>(F, W, rec, opacity, desc, pyramid, kept,
-                                                                 n_kept, t_final, n_frag, stream)));
+        TPK_DISPATCH_K(F.K, return (blend_impl<KC, __nv_bfloat16>(F, W, desc, pyramid, kept, n_kept, t_final,
+                                                                 n_frag, stream)));
     } else {
-        TPK_DISPATCH_K(F.K, return (blend_impl<KC, float>(F, W, rec, opacity, desc, pyramid, kept, n_kept,
-                                                         t_final, n_frag, stream)));
+        TPK_DISPATCH_K(F.K, return (blend_impl<KC, float>(F, W, desc, pyramid, kept, n_kept, t_final, n_frag,
+                                                         stream)));
     }
     return cudaErrorInvalidValue;
 }

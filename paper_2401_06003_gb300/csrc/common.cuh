@@ -31,6 +31,10 @@ struct Frame {
     int n_layers, K, D;
     int tile_w, tile_h;
     int n_tiles;
+    int tile_px;           // pixels per tile, tile_w * tile_h
+    int tile_threads;      // threads per tile CTA: tile_px rounded up to a warp
+    int chunk;             // tile-list entries merged per chunk by the tile kernels
+    int desc_vec;          // 1 if descriptors can be read 4 channels at a time
     int lw[kMaxLayers], lh[kMaxLayers];            // layer sizes W_L, H_L
     int tiles_x[kMaxLayers], tiles_y[kMaxLayers];  // tiles per layer row / column
     int tile_base[kMaxLayers + 1];                 // first tile id of each layer
@@ -43,8 +47,8 @@ struct Workspace {
     unsigned *tile_count;   // [n_tiles] (point, tile) pairs per tile
     unsigned *tile_off;     // [n_tiles + 1] exclusive scan of tile_count
     unsigned *tile_cursor;  // [n_tiles] fill cursors
-    unsigned *bucket_idx;   // [capacity] point index of each (point, tile) entry
-    float4 *bucket_rec;     // [capacity] point record of each entry
+    unsigned long long *bucket_key;  // [capacity] fragment key (z bits, point index) of each entry
+    float4 *bucket_pay;     // [capacity] (x, y, s, alpha) of the entry's point
     unsigned capacity;
 };
 
@@ -231,10 +235,11 @@ __device__ __forceinline__ float load_desc<__nv_bfloat16>(const __nv_bfloat16 *p
 cudaError_t launch_project_count(const Frame &F, const Workspace &W, long long n, const float *pos,
                                  const float *size_w, float4 *rec, cudaStream_t stream);
 cudaError_t launch_scan_fill(const Frame &F, const Workspace &W, long long n, const float4 *rec,
-                             cudaStream_t stream);
-cudaError_t launch_blend(const Frame &F, const Workspace &W, const float4 *rec, const float *opacity,
-                         const void *desc, int desc_dtype, float *pyramid, unsigned *kept, unsigned char *n_kept,
-                         float *t_final, unsigned *n_frag, cudaStream_t stream);
+                             const float *opacity, cudaStream_t stream);
+cudaError_t launch_blend(const Frame &F, const Workspace &W, const void *desc, int desc_dtype, float *pyramid,
+                         unsigned *kept, unsigned char *n_kept, float *t_final, unsigned *n_frag,
+                         cudaStream_t stream);
+size_t tile_smem_bytes(const Frame &F, bool backward);
 cudaError_t launch_backward(const Frame &F, const Workspace &W, long long n, const float4 *rec,
                             const float *opacity, const void *desc, int desc_dtype, const unsigned *kept,
                             const unsigned char *n_kept, const float *grad_pyramid, float *grad_pos,

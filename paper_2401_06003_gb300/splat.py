@@ -102,14 +102,14 @@ class Renderer:
         _lib.check("tp_project", st)
         return records
 
-    def splat_forward(self, records, ws):
-        st = self.lib.tp_splat_forward(ctypes.byref(self.cfg), ctypes.byref(self.cam), records.shape[0],
-                                       _ptr(records), _ptr(ws), ws.numel(), _stream(self.device))
-        _lib.check("tp_splat_forward", st)
-
-    def blend(self, records, opacity, desc, ws, store_lists=False, stats=False, pyramid=None):
+    def splat_forward(self, records, opacity, ws):
         n = records.shape[0]
         _need(opacity, torch.float32, (n,), "opacity", self.device)
+        st = self.lib.tp_splat_forward(ctypes.byref(self.cfg), ctypes.byref(self.cam), n, _ptr(records),
+                                       _ptr(opacity), _ptr(ws), ws.numel(), _stream(self.device))
+        _lib.check("tp_splat_forward", st)
+
+    def blend(self, n, desc, ws, store_lists=False, stats=False, pyramid=None):
         _need(desc, self.desc_dtype, (n, self.D), "desc", self.device)
         dev = self.device
         if pyramid is None:
@@ -121,9 +121,9 @@ class Renderer:
         if stats:
             t_final = torch.empty((self.P,), dtype=torch.float32, device=dev)
             n_frag = torch.empty((self.P,), dtype=torch.int32, device=dev)
-        st = self.lib.tp_blend(ctypes.byref(self.cfg), ctypes.byref(self.cam), n, _ptr(records), _ptr(opacity),
-                               _ptr(desc), _ptr(pyramid), _ptr(kept), _ptr(n_kept), _ptr(t_final), _ptr(n_frag),
-                               _ptr(ws), ws.numel(), _stream(dev))
+        st = self.lib.tp_blend(ctypes.byref(self.cfg), ctypes.byref(self.cam), n, _ptr(desc), _ptr(pyramid),
+                               _ptr(kept), _ptr(n_kept), _ptr(t_final), _ptr(n_frag), _ptr(ws), ws.numel(),
+                               _stream(dev))
         _lib.check("tp_blend", st)
         return pyramid, kept, n_kept, t_final, n_frag
 
@@ -160,8 +160,8 @@ class Renderer:
         if ws is None:
             ws = self.new_workspace(n)
         records = self.project(pos, size_w, ws)
-        self.splat_forward(records, ws)
-        pyramid, kept, n_kept, t_final, n_frag = self.blend(records, opacity, desc, ws, store_lists, stats)
+        self.splat_forward(records, opacity, ws)
+        pyramid, kept, n_kept, t_final, n_frag = self.blend(n, desc, ws, store_lists, stats)
         return Frame(pyramid, records, ws, kept, n_kept, t_final, n_frag)
 
     def backward(self, frame: Frame, opacity, desc, grad_pyramid):

@@ -61,6 +61,6 @@ def test_workspace_bytes_and_checks(lib):
                         None, 0, None)
     assert st == _lib.TP_ERR_UNSUPPORTED
     cam.znear = 0.0
-    st = lib.tp_splat_forward(ctypes.byref(cfg), ctypes.byref(cam), 10, None, None, 0, None)
+    st = lib.tp_splat_forward(ctypes.byref(cfg), ctypes.byref(cam), 10, None, None, None, 0, None)
     assert st == _lib.TP_ERR_INVALID_ARG
     assert lib.tp_status_string(_lib.TP_ERR_CAPACITY).decode().startswith("workspace")
