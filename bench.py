@@ -32,7 +32,7 @@ if ROOT not in sys.path:
 
 METRIC = "fwd+bwd ms/frame & Mpoints/s, 6M pts @1080p; % of HBM roofline"
 FALLBACK_HBM_GBS = 6800.0
-KERNELS_PER_STEP = 5  # k_project_count, k_scan_tiles, k_fill, k_tile_blend, k_tile_backward
+KERNELS_PER_STEP = 6  # k_project_count, k_tile_totals, k_scan_tiles, k_fill, k_tile_blend, k_tile_backward
 
 
 def parse_args():

@@ -109,9 +109,9 @@ WsLayout layout_for(const Frame &F, int64_t capacity)
     WsLayout w;
     const int64_t T = F.n_tiles;
     w.count = kAlign;
-    w.off = align_up(w.count + 4 * T);
+    w.off = align_up(w.count + 4 * T * tpk::kCopies);
     w.cursor = align_up(w.off + 4 * (T + 1));
-    w.key = align_up(w.cursor + 4 * T);
+    w.key = align_up(w.cursor + 4 * T * tpk::kCopies);
     w.pay = align_up(w.key + 8 * capacity);
     w.end = w.pay + 16 * capacity;
     return w;
@@ -249,6 +249,7 @@ tp_status tp_splat_backward(const tp_config *cfg, const tp_camera *cam, int64_t 
                   !aligned16(records)))
         return TP_ERR_INVALID_ARG;
     F.desc_vec = desc_vector_ok(cfg, desc);
+    F.grad_vec = (cfg->desc_dim % 4) == 0 && aligned16(grad_desc);
     return from_cuda(tpk::launch_backward(F, W, n, reinterpret_cast<const float4 *>(records), opacity, desc,
                                           cfg->desc_dtype, kept, n_kept, grad_pyramid, grad_pos, grad_size_w,
                                           grad_opacity, grad_desc, (cudaStream_t)stream));

@@ -8,6 +8,9 @@
 // count and fill passes make 1-2 global atomics per point instead of 4-8,
 // and the per-pixel lists are formed later in shared memory by the blend
 // kernel (blend.cu), which reads each tile's points with coalesced loads.
+// Each tile counter is split into kCopies copies (point i uses copy
+// i % kCopies) so that the thousands of points of a dense tile do not queue
+// on one address; k_tile_totals folds the copies back together.
 #include "common.cuh"
 
 namespace tpk {
@@ -50,11 +53,30 @@ __global__ void __launch_bounds__(kBlock) k_project_count(Frame F, Workspace W, 
             continue;
         }
         rec[i] = r;
-        for_each_tile(F, r, [&](int t) { atomicAdd(W.tile_count + t, 1u); });
+        const unsigned c = (unsigned)(i & (kCopies - 1));
+        for_each_tile(F, r, [&](int t) { atomicAdd(W.tile_count + (size_t)t * kCopies + c, 1u); });
     }
 }
 
-// Offset scan of the tile counts (one CTA; the tile count is small).
+// One warp per tile: the copies' exclusive prefix becomes each copy's fill
+// cursor, and the tile's total goes to tile_off[t] for the offset scan.
+__global__ void __launch_bounds__(kBlock) k_tile_totals(Frame F, Workspace W)
+{
+    const int t = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (t >= F.n_tiles) return;
+    const unsigned v = W.tile_count[(size_t)t * kCopies + lane];
+    unsigned x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    W.tile_cursor[(size_t)t * kCopies + lane] = x - v;
+    if (lane == 31) W.tile_off[t] = x;
+}
+
+// Offset scan of the tile totals, in place (one CTA; the tile count is small).
 __global__ void __launch_bounds__(1024) k_scan_tiles(Frame F, Workspace W)
 {
     __shared__ unsigned warp_tot[32];
@@ -63,7 +85,7 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Frame F, Workspace W)
     const int beg = min(T, (int)threadIdx.x * per);
     const int end = min(T, beg + per);
     unsigned sum = 0;
-    for (int q = beg; q < end; ++q) sum += W.tile_count[q];
+    for (int q = beg; q < end; ++q) sum += W.tile_off[q];
     // inclusive warp scan
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned v = sum;
@@ -86,9 +108,8 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Frame F, Workspace W)
     __syncthreads();
     unsigned run = v - sum + (warp > 0 ? warp_tot[warp - 1] : 0u);
     for (int q = beg; q < end; ++q) {
-        const unsigned c = W.tile_count[q];
+        const unsigned c = W.tile_off[q];
         W.tile_off[q] = run;
-        W.tile_cursor[q] = 0u;
         run += c;
     }
     if (threadIdx.x == 0) {
@@ -109,8 +130,9 @@ __global__ void __launch_bounds__(kBlock) k_fill(Frame F, Workspace W, long long
         if (!(r.z > 0.0f)) continue;  // culled
         const unsigned long long key = frag_key(r.z, (unsigned)i);
         const float4 pay = make_float4(r.x, r.y, r.w, __ldg(opacity + i));
+        const unsigned c = (unsigned)(i & (kCopies - 1));
         for_each_tile(F, r, [&](int t) {
-            const unsigned e = W.tile_off[t] + atomicAdd(W.tile_cursor + t, 1u);
+            const unsigned e = W.tile_off[t] + atomicAdd(W.tile_cursor + (size_t)t * kCopies + c, 1u);
             if (e < W.capacity) {
                 W.bucket_key[e] = key;
                 W.bucket_pay[e] = pay;
@@ -132,7 +154,7 @@ cudaError_t launch_project_count(const Frame &F, const Workspace &W, long long n
 {
     cudaError_t e = cudaMemsetAsync(W.status, 0, sizeof(unsigned), stream);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(W.tile_count, 0, sizeof(unsigned) * (size_t)F.n_tiles, stream);
+    e = cudaMemsetAsync(W.tile_count, 0, sizeof(unsigned) * kCopies * (size_t)F.n_tiles, stream);
     if (e != cudaSuccess) return e;
     if (n == 0) return cudaSuccess;
     k_project_count<<<grid_for(n), kBlock, 0, stream>>>(F, W, n, pos, size_w, rec);
@@ -142,8 +164,12 @@ cudaError_t launch_project_count(const Frame &F, const Workspace &W, long long n
 cudaError_t launch_scan_fill(const Frame &F, const Workspace &W, long long n, const float4 *rec,
                              const float *opacity, cudaStream_t stream)
 {
-    k_scan_tiles<<<1, 1024, 0, stream>>>(F, W);
+    const long long threads = (long long)F.n_tiles * 32;
+    k_tile_totals<<<(int)((threads + kBlock - 1) / kBlock), kBlock, 0, stream>>>(F, W);
     cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_scan_tiles<<<1, 1024, 0, stream>>>(F, W);
+    e = cudaGetLastError();
     if (e != cudaSuccess || n == 0) return e;
     k_fill<<<grid_for(n), kBlock, 0, stream>>>(F, W, n, rec, opacity);
     return cudaGetLastError();

@@ -339,7 +339,31 @@ __device__ __forceinline__ void adjoint_fragment(const Frame &F, int L, int j, i
 
 constexpr int kMaxGradD = 64;
 
+// Adds v to four consecutive floats (16-byte aligned) with one vector atomic.
+__device__ __forceinline__ void atomic_add4(float *p, float4 v)
+{
+    atomicAdd(reinterpret_cast<float4 *>(p), v);
+}
+
+// Rank of `key` in the pixel's sorted kept list (slot-major, n entries), or -1.
+__device__ __forceinline__ int kept_rank(const unsigned long long *kk, int TP, int px, int n, unsigned long long key)
+{
+    if (n == 0 || key > kk[(n - 1) * TP + px]) return -1;
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (kk[mid * TP + px] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return kk[lo * TP + px] == key ? lo : -1;
+}
+
 // Backward with the lists rebuilt from the workspace's tile lists.
+//   phase A, one thread per pixel: forward weights, then the back-to-front
+//     adjoint of the blend, leaving dL/dgamma_m and T_m gamma_m per kept slot;
+//   phase B, one thread per tile-list entry: the entry's point finds its kept
+//     fragments in the (at most four) pixels it touches, sums their
+//     contributions and scatters them with one set of atomics.
 template <int K, typename DescT>
 __global__ void k_tile_backward(Frame F, Workspace W, const DescT *__restrict__ desc,
                                 const float *__restrict__ grad_pyr, float *__restrict__ gpos, float *__restrict__ gsw,
@@ -351,32 +375,113 @@ __global__ void k_tile_backward(Frame F, Workspace W, const DescT *__restrict__ 
     const TileGeom g = tile_geom(F, tile);
     unsigned nfr;
     const int nk = build_topk<K>(F, W, tile, g, S, &nfr);
-    const int TP = F.tile_px, tid = threadIdx.x, L = g.L;
-    if (tid >= TP || nk == 0) return;
-    const int j = g.x0 + tid % F.tile_w, k = g.y0 + tid / F.tile_w;
-    if (j >= F.lw[L] || k >= F.lh[L]) return;
-    const long long pix = F.pix_base[L] + (long long)k * F.lw[L] + j;
-    float *gam = S.scratch;                       // [K][TP]
-    float *Tm = S.scratch + (size_t)K * TP;       // [K][TP]
-    float T = 1.0f;
-    for (int m = 0; m < nk; ++m) {
-        const float4 pay = W.bucket_pay[S.tk_e[m * TP + tid]];
-        const FragW w = frag_weights(F, pay.x, pay.y, pay.z, L, j, k);
-        const float gm = w.wx * w.wy * w.iota * pay.w;
-        gam[m * TP + tid] = gm;
-        Tm[m * TP + tid] = T;
-        T = T * (1.0f - gm);
+    const int TP = F.tile_px, tid = threadIdx.x, L = g.L, D = F.D;
+    float *sc_dg = S.scratch;                     // [K][TP] dL/dgamma_m
+    float *sc_tg = S.scratch + (size_t)K * TP;    // [K][TP] T_m gamma_m
+    unsigned *n_top = S.cnt;                      // [TP] kept count per pixel
+    if (tid < TP) {
+        const int j = g.x0 + tid % F.tile_w, k = g.y0 + tid / F.tile_w;
+        const bool in = j < F.lw[L] && k < F.lh[L];
+        n_top[tid] = in ? (unsigned)nk : 0u;
+        if (in && nk > 0) {
+            const long long pix = F.pix_base[L] + (long long)k * F.lw[L] + j;
+            float T = 1.0f;
+            for (int m = 0; m < nk; ++m) {
+                const float4 pay = W.bucket_pay[S.tk_e[m * TP + tid]];
+                const FragW w = frag_weights(F, pay.x, pay.y, pay.z, L, j, k);
+                const float gm = w.wx * w.wy * w.iota * pay.w;
+                sc_dg[m * TP + tid] = gm;  // gamma_m for now
+                sc_tg[m * TP + tid] = T;   // T_m for now
+                T = T * (1.0f - gm);
+            }
+            float G[kMaxGradD];
+            for (int d = 0; d < D; ++d) G[d] = __ldg(grad_pyr + pix * D + d);
+            float R = 0.0f;
+            for (int m = nk - 1; m >= 0; --m) {
+                const unsigned i = (unsigned)(S.tk_key[m * TP + tid] & 0xFFFFFFFFull);
+                float gdot = 0.0f;
+                for (int d0 = 0; d0 < D; d0 += 4) {
+                    const float4 t = load_desc4(desc, i, D, d0, F.desc_vec);
+                    gdot += G[d0] * t.x;
+                    if (d0 + 1 < D) gdot += G[d0 + 1] * t.y;
+                    if (d0 + 2 < D) gdot += G[d0 + 2] * t.z;
+                    if (d0 + 3 < D) gdot += G[d0 + 3] * t.w;
+                }
+                const float gm = sc_dg[m * TP + tid], Tm = sc_tg[m * TP + tid];
+                sc_dg[m * TP + tid] = Tm * (gdot - R);
+                sc_tg[m * TP + tid] = Tm * gm;
+                R = gm * gdot + (1.0f - gm) * R;
+            }
+        }
+    } else {
+        n_top[tid] = 0u;
     }
-    float G[kMaxGradD];
-    const int D = F.D;
-    for (int d = 0; d < D; ++d) G[d] = __ldg(grad_pyr + pix * D + d);
-    float R = 0.0f;
-    for (int m = nk - 1; m >= 0; --m) {
-        const unsigned long long key = S.tk_key[m * TP + tid];
-        const float4 pay = W.bucket_pay[S.tk_e[m * TP + tid]];
-        adjoint_fragment<DescT>(F, L, j, k, (unsigned)(key & 0xFFFFFFFFull), pay.x, pay.y,
-                                __uint_as_float((unsigned)(key >> 32)), pay.z, pay.w, gam[m * TP + tid],
-                                Tm[m * TP + tid], G, R, desc, gpos, gsw, gop, gdesc);
+    __syncthreads();
+    unsigned end = W.tile_off[tile + 1];
+    if (end > W.capacity) end = W.capacity;
+    unsigned beg = W.tile_off[tile];
+    if (beg > end) beg = end;
+    for (unsigned e = beg + tid; e < end; e += blockDim.x) {
+        const unsigned long long key = W.bucket_key[e];
+        const float4 pay = W.bucket_pay[e];
+        int tap_px[4], tap_m[4], nt = 0;
+        entry_taps(F, g, pay, [&](int px) {
+            const int m = kept_rank(S.tk_key, TP, px, (int)n_top[px], key);
+            if (m >= 0) {
+                tap_px[nt] = px;
+                tap_m[nt] = m;
+                ++nt;
+            }
+        });
+        if (nt == 0) continue;
+        const unsigned i = (unsigned)(key & 0xFFFFFFFFull);
+        const float z = __uint_as_float((unsigned)(key >> 32));
+        float g_al = 0.0f, gx = 0.0f, gy = 0.0f, gs = 0.0f;
+        for (int q = 0; q < nt; ++q) {
+            const int px = tap_px[q], m = tap_m[q];
+            const int j = g.x0 + px % F.tile_w, k = g.y0 + px / F.tile_w;
+            const FragW w = frag_weights(F, pay.x, pay.y, pay.z, L, j, k);
+            const float dg = sc_dg[m * TP + px];
+            const float beta = w.wx * w.wy;
+            g_al += dg * beta * w.iota;
+            const float dw = dg * pay.w;
+            gx += dw * w.wy * w.iota * w.dwx;
+            gy += dw * w.wx * w.iota * w.dwy;
+            gs += dw * beta * w.diota;
+        }
+        // descriptor gradient: sum over taps of T_m gamma_m G(pixel)
+        float *gd = gdesc + (long long)i * D;
+        for (int d0 = 0; d0 < D; d0 += 4) {
+            float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            for (int q = 0; q < nt; ++q) {
+                const int px = tap_px[q];
+                const long long pix = F.pix_base[L] + (long long)(g.y0 + px / F.tile_w) * F.lw[L] +
+                                      (g.x0 + px % F.tile_w);
+                const float tg = sc_tg[tap_m[q] * TP + px];
+                const float *Gp = grad_pyr + pix * D + d0;
+                a.x += tg * __ldg(Gp);
+                if (d0 + 1 < D) a.y += tg * __ldg(Gp + 1);
+                if (d0 + 2 < D) a.z += tg * __ldg(Gp + 2);
+                if (d0 + 3 < D) a.w += tg * __ldg(Gp + 3);
+            }
+            if (F.grad_vec) {
+                atomic_add4(gd + d0, a);
+            } else {
+                atomicAdd(gd + d0, a.x);
+                if (d0 + 1 < D) atomicAdd(gd + d0 + 1, a.y);
+                if (d0 + 2 < D) atomicAdd(gd + d0 + 2, a.z);
+                if (d0 + 3 < D) atomicAdd(gd + d0 + 3, a.w);
+            }
+        }
+        atomicAdd(gop + i, g_al);
+        const float iz = 1.0f / z;
+        const float dXc = gx * F.fx * iz;
+        const float dYc = gy * F.fy * iz;
+        const float dZc = -(gx * (pay.x - F.cx) + gy * (pay.y - F.cy) + gs * pay.z) * iz;
+        atomicAdd(gsw + i, gs * F.fx * iz);
+        atomicAdd(gpos + 3 * (long long)i + 0, F.R[0] * dXc + F.R[3] * dYc + F.R[6] * dZc);
+        atomicAdd(gpos + 3 * (long long)i + 1, F.R[1] * dXc + F.R[4] * dYc + F.R[7] * dZc);
+        atomicAdd(gpos + 3 * (long long)i + 2, F.R[2] * dXc + F.R[5] * dYc + F.R[8] * dZc);
     }
 }
 

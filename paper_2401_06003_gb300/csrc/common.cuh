@@ -35,6 +35,7 @@ struct Frame {
     int tile_threads;      // threads per tile CTA: tile_px rounded up to a warp
     int chunk;             // tile-list entries merged per chunk by the tile kernels
     int desc_vec;          // 1 if descriptors can be read 4 channels at a time
+    int grad_vec;          // 1 if descriptor gradients can take 4-channel vector atomics
     int lw[kMaxLayers], lh[kMaxLayers];            // layer sizes W_L, H_L
     int tiles_x[kMaxLayers], tiles_y[kMaxLayers];  // tiles per layer row / column
     int tile_base[kMaxLayers + 1];                 // first tile id of each layer
@@ -42,11 +43,16 @@ struct Frame {
 };
 
 // Device pointers into the caller's workspace.
+// Every tile counter exists in kCopies copies; point i uses copy i % kCopies.
+// Hot tiles (thousands of points near the horizon) would otherwise serialise
+// their atomics on one address.
+constexpr int kCopies = 32;
+
 struct Workspace {
     unsigned *status;       // [1] TP_FLAG_* bits
-    unsigned *tile_count;   // [n_tiles] (point, tile) pairs per tile
-    unsigned *tile_off;     // [n_tiles + 1] exclusive scan of tile_count
-    unsigned *tile_cursor;  // [n_tiles] fill cursors
+    unsigned *tile_count;   // [n_tiles][kCopies] (point, tile) pairs per tile and copy
+    unsigned *tile_off;     // [n_tiles + 1] first entry of each tile's list
+    unsigned *tile_cursor;  // [n_tiles][kCopies] fill cursor of each copy (relative to tile_off)
     unsigned long long *bucket_key;  // [capacity] fragment key (z bits, point index) of each entry
     float4 *bucket_pay;     // [capacity] (x, y, s, alpha) of the entry's point
     unsigned capacity;
