@@ -9,7 +9,8 @@
 //   3. scatters the chunk's fragment keys (z, i) into per-pixel runs in
 //      shared memory,
 //   4. lets each thread merge its own pixel's run into that pixel's sorted
-//      list of the K smallest keys (a private insertion sort, no atomics).
+//      list of the K smallest keys, held in the thread's registers (a
+//      branch-free compare-exchange insertion, no atomics, no shared memory).
 // After the last chunk every pixel holds exactly the K front-most fragments
 // of its full list in (depth, index) order -- the list the paper sorts per
 // pixel and clamps to 16 elements (Sec. 3.2) -- without ever storing the full
@@ -18,7 +19,7 @@
 //
 // The backward kernels run the adjoint of the blend per pixel back to front
 // over the kept list (division-free recurrence) and scatter the point
-// gradients with float atomics.
+// gradients with float atomics (one vector atomic per descriptor row).
 #include "common.cuh"
 
 namespace tpk {
@@ -37,41 +38,24 @@ __device__ __forceinline__ TileGeom tile_geom(const Frame &F, int tile)
     return g;
 }
 
-// Shared-memory layout of a tile CTA (offsets in bytes, all 16-aligned).
+// Shared-memory layout of a tile CTA (16-byte aligned pieces): the current
+// chunk's fragments grouped by pixel, and the per-pixel counters.
 struct TileSmem {
-    unsigned long long *tk_key;  // [K][tile_px]  sorted kept keys, slot-major
-    unsigned *tk_e;              // [K][tile_px]  workspace entry of each kept key
-    unsigned long long *ck;      // [4 chunk]     chunk fragment keys, grouped by pixel
-    unsigned *ce;                // [4 chunk]     chunk fragment entries
-    float *scratch;              // aliases ck/ce after the last chunk
+    unsigned long long *ck;      // [4 chunk] chunk fragment keys, grouped by pixel
+    unsigned *ce;                // [4 chunk] chunk fragment entries
     unsigned *cnt, *off, *cur;   // [tile_threads]
     unsigned *wsum;              // [32]
 };
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
-__host__ __device__ inline size_t chunk_area_bytes(const Frame &F, bool backward)
-{
-    size_t a = (size_t)4 * F.chunk * (sizeof(unsigned long long) + sizeof(unsigned));
-    // scratch after the chunks: the blend keeps T_m gamma_m, the adjoint gamma_m and T_m
-    const size_t s = (size_t)(backward ? 2 : 1) * F.K * F.tile_px * sizeof(float);
-    return align16(a > s ? a : s);
-}
-
-__device__ __forceinline__ TileSmem carve(const Frame &F, unsigned char *base, bool backward)
+__device__ __forceinline__ TileSmem carve(const Frame &F, unsigned char *base)
 {
     TileSmem m;
-    const size_t TP = F.tile_px, NT = F.tile_threads;
-    size_t o = 0;
-    m.tk_key = reinterpret_cast<unsigned long long *>(base + o);
-    o += align16(TP * F.K * sizeof(unsigned long long));
-    m.tk_e = reinterpret_cast<unsigned *>(base + o);
-    o += align16(TP * F.K * sizeof(unsigned));
-    m.ck = reinterpret_cast<unsigned long long *>(base + o);
-    m.ce = reinterpret_cast<unsigned *>(base + o + (size_t)4 * F.chunk * sizeof(unsigned long long));
-    m.scratch = reinterpret_cast<float *>(base + o);
-    o += chunk_area_bytes(F, backward);
-    m.cnt = reinterpret_cast<unsigned *>(base + o);
+    const size_t NT = F.tile_threads;
+    m.ck = reinterpret_cast<unsigned long long *>(base);
+    m.ce = reinterpret_cast<unsigned *>(base + (size_t)4 * F.chunk * sizeof(unsigned long long));
+    m.cnt = reinterpret_cast<unsigned *>(base + align16((size_t)4 * F.chunk * 12));
     m.off = m.cnt + NT;
     m.cur = m.off + NT;
     m.wsum = m.cur + NT;
@@ -80,9 +64,8 @@ __device__ __forceinline__ TileSmem carve(const Frame &F, unsigned char *base, b
 
 size_t tile_smem_bytes(const Frame &F, bool backward)
 {
-    const size_t TP = F.tile_px, NT = F.tile_threads;
-    return align16(TP * F.K * sizeof(unsigned long long)) + align16(TP * F.K * sizeof(unsigned)) +
-           chunk_area_bytes(F, backward) + (3 * NT + 32) * sizeof(unsigned);
+    (void)backward;
+    return align16((size_t)4 * F.chunk * 12) + (3 * (size_t)F.tile_threads + 32) * sizeof(unsigned);
 }
 
 // Exclusive scan of v over the CTA (blockDim.x <= 1024, a multiple of 32).
@@ -134,44 +117,55 @@ __device__ __forceinline__ void entry_taps(const Frame &F, const TileGeom &g, co
     }
 }
 
-// Insert (key, e) into this thread's sorted list of at most K keys.
+// A pixel's kept list: the K smallest keys seen so far in ascending order,
+// with the workspace entry of each; empty slots hold kEmptyKey.
 template <int K>
-__device__ __forceinline__ void topk_insert(unsigned long long *kk, unsigned *ke, int TP, int px, int &n_top,
-                                            unsigned long long key, unsigned e)
-{
-    int pos;
-    if (n_top == K) {
-        if (key >= kk[(K - 1) * TP + px]) return;
-        pos = K - 1;
-    } else {
-        pos = n_top++;
-    }
-    while (pos > 0) {
-        const unsigned long long prev = kk[(pos - 1) * TP + px];
-        if (prev < key) break;
-        kk[pos * TP + px] = prev;
-        ke[pos * TP + px] = ke[(pos - 1) * TP + px];
-        --pos;
-    }
-    kk[pos * TP + px] = key;
-    ke[pos * TP + px] = e;
-}
+struct TopK {
+    unsigned long long key[K];
+    unsigned e[K];
 
-// Builds every pixel's kept list.  Thread t owns pixel t (t < tile_px).
-// Returns the kept count of the thread's pixel; *nfrag gets its candidates.
+    __device__ __forceinline__ void clear()
+    {
+#pragma unroll
+        for (int m = 0; m < K; ++m) {
+            key[m] = kEmptyKey;
+            e[m] = 0u;
+        }
+    }
+
+    // Compare-exchange chain: after slot m, slots 0..m hold the m+1 smallest
+    // of (old slots 0..m, new key) in order; the largest key falls off the end.
+    __device__ __forceinline__ void insert(unsigned long long k, unsigned ee)
+    {
+        if (k >= key[K - 1]) return;
+#pragma unroll
+        for (int m = 0; m < K; ++m) {
+            const bool lt = k < key[m];
+            const unsigned long long tk = key[m];
+            const unsigned te = e[m];
+            key[m] = lt ? k : tk;
+            e[m] = lt ? ee : te;
+            k = lt ? tk : k;
+            ee = lt ? te : ee;
+        }
+    }
+};
+
+// Builds the kept list of the thread's pixel (thread t owns pixel t of the
+// tile, t < tile_px); returns the kept count, *nfrag gets the candidates.
 template <int K>
 __device__ int build_topk(const Frame &F, const Workspace &W, int tile, const TileGeom &g, const TileSmem &S,
-                          unsigned *nfrag)
+                          TopK<K> &top, unsigned *nfrag)
 {
     const int TP = F.tile_px, tid = threadIdx.x, NT = blockDim.x;
     const bool owner = tid < TP;
+    top.clear();
     S.cnt[tid] = 0u;
     S.cur[tid] = 0u;
     unsigned end = W.tile_off[tile + 1];
     if (end > W.capacity) end = W.capacity;
     unsigned beg = W.tile_off[tile];
     if (beg > end) beg = end;
-    int n_top = 0;
     unsigned nfr = 0;
     __syncthreads();
     for (unsigned c0 = beg; c0 < end; c0 += (unsigned)F.chunk) {
@@ -193,7 +187,7 @@ __device__ int build_topk(const Frame &F, const Workspace &W, int tile, const Ti
         __syncthreads();
         if (owner) {
             const unsigned a = S.off[tid];
-            for (unsigned q = a; q < a + my; ++q) topk_insert<K>(S.tk_key, S.tk_e, TP, tid, n_top, S.ck[q], S.ce[q]);
+            for (unsigned q = a; q < a + my; ++q) top.insert(S.ck[q], S.ce[q]);
             nfr += my;
         }
         S.cnt[tid] = 0u;
@@ -201,7 +195,7 @@ __device__ int build_topk(const Frame &F, const Workspace &W, int tile, const Ti
         __syncthreads();
     }
     *nfrag = nfr;
-    return n_top;
+    return nfr < (unsigned)K ? (int)nfr : K;
 }
 
 // beta * iota of a point with payload (x, y, s, alpha) at layer-L pixel (j, k),
@@ -249,65 +243,89 @@ __global__ void k_tile_blend(Frame F, Workspace W, const DescT *__restrict__ des
                              float *__restrict__ t_final, unsigned *__restrict__ n_frag)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const TileSmem S = carve(F, smem_raw, false);
+    const TileSmem S = carve(F, smem_raw);
     const int tile = blockIdx.x;
     const TileGeom g = tile_geom(F, tile);
+    TopK<K> top;
     unsigned nfr;
-    const int nk = build_topk<K>(F, W, tile, g, S, &nfr);
+    int nk = build_topk<K>(F, W, tile, g, S, top, &nfr);
     const int TP = F.tile_px, tid = threadIdx.x, L = g.L;
-    if (tid >= TP) return;
     const int j = g.x0 + tid % F.tile_w, k = g.y0 + tid / F.tile_w;
-    if (j >= F.lw[L] || k >= F.lh[L]) return;
+    const bool active = tid < TP && j < F.lw[L] && k < F.lh[L];
+    if (!active) nk = 0;
+    const int nk_warp = __reduce_max_sync(0xffffffffu, nk);
     const long long pix = F.pix_base[L] + (long long)k * F.lw[L] + j;
     // front to back: weights T_m gamma_m (Eq. 6-7)
+    float wgt[K];
     float T = 1.0f;
-    for (int m = 0; m < nk; ++m) {
-        const float4 pay = W.bucket_pay[S.tk_e[m * TP + tid]];
-        const FragW w = frag_weights(F, pay.x, pay.y, pay.z, L, j, k);
-        const float gam = w.wx * w.wy * w.iota * pay.w;
-        S.scratch[m * TP + tid] = T * gam;
-        T = T * (1.0f - gam);
+#pragma unroll
+    for (int m = 0; m < K; ++m) {
+        wgt[m] = 0.0f;
+        if (m >= nk_warp) break;
+        if (m < nk) {
+            const float4 pay = W.bucket_pay[top.e[m]];
+            const FragW w = frag_weights(F, pay.x, pay.y, pay.z, L, j, k);
+            const float gam = w.wx * w.wy * w.iota * pay.w;
+            wgt[m] = T * gam;
+            T = T * (1.0f - gam);
+        }
     }
     const int D = F.D;
     for (int d0 = 0; d0 < D; d0 += 4) {
         float4 c = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        for (int m = 0; m < nk; ++m) {
-            const unsigned i = (unsigned)(S.tk_key[m * TP + tid] & 0xFFFFFFFFull);
-            const float wgt = S.scratch[m * TP + tid];
-            const float4 t = load_desc4(desc, i, D, d0, F.desc_vec);
-            c.x += wgt * t.x;
-            c.y += wgt * t.y;
-            c.z += wgt * t.z;
-            c.w += wgt * t.w;
+#pragma unroll
+        for (int m = 0; m < K; ++m) {
+            if (m >= nk_warp) break;
+            if (m < nk) {
+                const float4 t = load_desc4(desc, (unsigned)(top.key[m] & 0xFFFFFFFFull), D, d0, F.desc_vec);
+                c.x += wgt[m] * t.x;
+                c.y += wgt[m] * t.y;
+                c.z += wgt[m] * t.z;
+                c.w += wgt[m] * t.w;
+            }
         }
-        float *out = pyramid + pix * D + d0;
-        if (F.desc_vec) {
-            *reinterpret_cast<float4 *>(out) = c;
-        } else {
-            const float cv[4] = {c.x, c.y, c.z, c.w};
-            for (int q = 0; q < 4 && d0 + q < D; ++q) out[q] = cv[q];
+        if (active) {
+            float *out = pyramid + pix * D + d0;
+            if (F.desc_vec) {
+                *reinterpret_cast<float4 *>(out) = c;
+            } else {
+                const float cv[4] = {c.x, c.y, c.z, c.w};
+                for (int q = 0; q < 4 && d0 + q < D; ++q) out[q] = cv[q];
+            }
         }
     }
+    if (!active) return;
     if (kept) {
+#pragma unroll
         for (int m = 0; m < K; ++m)
-            kept[pix * K + m] = m < nk ? (unsigned)(S.tk_key[m * TP + tid] & 0xFFFFFFFFull) : kNoPoint;
+            kept[pix * K + m] = m < nk ? (unsigned)(top.key[m] & 0xFFFFFFFFull) : kNoPoint;
     }
     if (n_kept) n_kept[pix] = (unsigned char)nk;
     if (t_final) t_final[pix] = T;
     if (n_frag) n_frag[pix] = nfr;
 }
 
+constexpr int kMaxGradD = 64;
+
+// Adds v to four consecutive floats (16-byte aligned) with one vector atomic.
+__device__ __forceinline__ void atomic_add4(float *p, float4 v)
+{
+    atomicAdd(reinterpret_cast<float4 *>(p), v);
+}
+
 // Adjoint of one kept fragment, given its forward quantities; scatters the
 // point gradients.  G is the pixel's dL/dC; R the running back-to-front term.
 template <typename DescT>
 __device__ __forceinline__ void adjoint_fragment(const Frame &F, int L, int j, int k, unsigned i, float x, float y,
-                                                 float z, float s, float al, float gam, float Tm, const float *G,
-                                                 float &R, const DescT *__restrict__ desc, float *__restrict__ gpos,
+                                                 float z, float s, float al, float Tm, const float *G, float &R,
+                                                 const DescT *__restrict__ desc, float *__restrict__ gpos,
                                                  float *__restrict__ gsw, float *__restrict__ gop,
                                                  float *__restrict__ gdesc)
 {
     const int D = F.D;
     const FragW w = frag_weights(F, x, y, s, L, j, k);
+    const float beta = w.wx * w.wy;
+    const float gam = beta * w.iota * al;
     float gdot = 0.0f;
     for (int d0 = 0; d0 < D; d0 += 4) {
         const float4 t = load_desc4(desc, i, D, d0, F.desc_vec);
@@ -320,8 +338,12 @@ __device__ __forceinline__ void adjoint_fragment(const Frame &F, int L, int j, i
     R = gam * gdot + (1.0f - gam) * R;
     const float tg = Tm * gam;
     float *gd = gdesc + (long long)i * D;
-    for (int d = 0; d < D; ++d) atomicAdd(gd + d, tg * G[d]);
-    const float beta = w.wx * w.wy;
+    if (F.grad_vec) {
+        for (int d0 = 0; d0 < D; d0 += 4)
+            atomic_add4(gd + d0, make_float4(tg * G[d0], tg * G[d0 + 1], tg * G[d0 + 2], tg * G[d0 + 3]));
+    } else {
+        for (int d = 0; d < D; ++d) atomicAdd(gd + d, tg * G[d]);
+    }
     atomicAdd(gop + i, dg * beta * w.iota);
     const float dw = dg * al;
     const float gx = dw * w.wy * w.iota * w.dwx;
@@ -337,151 +359,52 @@ __device__ __forceinline__ void adjoint_fragment(const Frame &F, int L, int j, i
     atomicAdd(gpos + 3 * (long long)i + 2, F.R[2] * dXc + F.R[5] * dYc + F.R[8] * dZc);
 }
 
-constexpr int kMaxGradD = 64;
-
-// Adds v to four consecutive floats (16-byte aligned) with one vector atomic.
-__device__ __forceinline__ void atomic_add4(float *p, float4 v)
-{
-    atomicAdd(reinterpret_cast<float4 *>(p), v);
-}
-
-// Rank of `key` in the pixel's sorted kept list (slot-major, n entries), or -1.
-__device__ __forceinline__ int kept_rank(const unsigned long long *kk, int TP, int px, int n, unsigned long long key)
-{
-    if (n == 0 || key > kk[(n - 1) * TP + px]) return -1;
-    int lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (kk[mid * TP + px] < key) lo = mid + 1;
-        else hi = mid;
-    }
-    return kk[lo * TP + px] == key ? lo : -1;
-}
-
-// Backward with the lists rebuilt from the workspace's tile lists.
-//   phase A, one thread per pixel: forward weights, then the back-to-front
-//     adjoint of the blend, leaving dL/dgamma_m and T_m gamma_m per kept slot;
-//   phase B, one thread per tile-list entry: the entry's point finds its kept
-//     fragments in the (at most four) pixels it touches, sums their
-//     contributions and scatters them with one set of atomics.
+// Backward with the lists rebuilt from the workspace's tile lists: each
+// pixel thread runs the adjoint of its own blend back to front.
 template <int K, typename DescT>
 __global__ void k_tile_backward(Frame F, Workspace W, const DescT *__restrict__ desc,
                                 const float *__restrict__ grad_pyr, float *__restrict__ gpos, float *__restrict__ gsw,
                                 float *__restrict__ gop, float *__restrict__ gdesc)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const TileSmem S = carve(F, smem_raw, true);
+    const TileSmem S = carve(F, smem_raw);
     const int tile = blockIdx.x;
     const TileGeom g = tile_geom(F, tile);
+    TopK<K> top;
     unsigned nfr;
-    const int nk = build_topk<K>(F, W, tile, g, S, &nfr);
+    int nk = build_topk<K>(F, W, tile, g, S, top, &nfr);
     const int TP = F.tile_px, tid = threadIdx.x, L = g.L, D = F.D;
-    float *sc_dg = S.scratch;                     // [K][TP] dL/dgamma_m
-    float *sc_tg = S.scratch + (size_t)K * TP;    // [K][TP] T_m gamma_m
-    unsigned *n_top = S.cnt;                      // [TP] kept count per pixel
-    if (tid < TP) {
-        const int j = g.x0 + tid % F.tile_w, k = g.y0 + tid / F.tile_w;
-        const bool in = j < F.lw[L] && k < F.lh[L];
-        n_top[tid] = in ? (unsigned)nk : 0u;
-        if (in && nk > 0) {
-            const long long pix = F.pix_base[L] + (long long)k * F.lw[L] + j;
-            float T = 1.0f;
-            for (int m = 0; m < nk; ++m) {
-                const float4 pay = W.bucket_pay[S.tk_e[m * TP + tid]];
-                const FragW w = frag_weights(F, pay.x, pay.y, pay.z, L, j, k);
-                const float gm = w.wx * w.wy * w.iota * pay.w;
-                sc_dg[m * TP + tid] = gm;  // gamma_m for now
-                sc_tg[m * TP + tid] = T;   // T_m for now
-                T = T * (1.0f - gm);
-            }
-            float G[kMaxGradD];
-            for (int d = 0; d < D; ++d) G[d] = __ldg(grad_pyr + pix * D + d);
-            float R = 0.0f;
-            for (int m = nk - 1; m >= 0; --m) {
-                const unsigned i = (unsigned)(S.tk_key[m * TP + tid] & 0xFFFFFFFFull);
-                float gdot = 0.0f;
-                for (int d0 = 0; d0 < D; d0 += 4) {
-                    const float4 t = load_desc4(desc, i, D, d0, F.desc_vec);
-                    gdot += G[d0] * t.x;
-                    if (d0 + 1 < D) gdot += G[d0 + 1] * t.y;
-                    if (d0 + 2 < D) gdot += G[d0 + 2] * t.z;
-                    if (d0 + 3 < D) gdot += G[d0 + 3] * t.w;
-                }
-                const float gm = sc_dg[m * TP + tid], Tm = sc_tg[m * TP + tid];
-                sc_dg[m * TP + tid] = Tm * (gdot - R);
-                sc_tg[m * TP + tid] = Tm * gm;
-                R = gm * gdot + (1.0f - gm) * R;
-            }
-        }
-    } else {
-        n_top[tid] = 0u;
-    }
-    __syncthreads();
-    unsigned end = W.tile_off[tile + 1];
-    if (end > W.capacity) end = W.capacity;
-    unsigned beg = W.tile_off[tile];
-    if (beg > end) beg = end;
-    for (unsigned e = beg + tid; e < end; e += blockDim.x) {
-        const unsigned long long key = W.bucket_key[e];
-        const float4 pay = W.bucket_pay[e];
-        int tap_px[4], tap_m[4], nt = 0;
-        entry_taps(F, g, pay, [&](int px) {
-            const int m = kept_rank(S.tk_key, TP, px, (int)n_top[px], key);
-            if (m >= 0) {
-                tap_px[nt] = px;
-                tap_m[nt] = m;
-                ++nt;
-            }
-        });
-        if (nt == 0) continue;
-        const unsigned i = (unsigned)(key & 0xFFFFFFFFull);
-        const float z = __uint_as_float((unsigned)(key >> 32));
-        float g_al = 0.0f, gx = 0.0f, gy = 0.0f, gs = 0.0f;
-        for (int q = 0; q < nt; ++q) {
-            const int px = tap_px[q], m = tap_m[q];
-            const int j = g.x0 + px % F.tile_w, k = g.y0 + px / F.tile_w;
+    const int j = g.x0 + tid % F.tile_w, k = g.y0 + tid / F.tile_w;
+    const bool active = tid < TP && j < F.lw[L] && k < F.lh[L];
+    if (!active) nk = 0;
+    const int nk_warp = __reduce_max_sync(0xffffffffu, nk);
+    if (nk_warp == 0) return;
+    const long long pix = F.pix_base[L] + (long long)k * F.lw[L] + j;
+    float Tm[K];
+    float T = 1.0f;
+#pragma unroll
+    for (int m = 0; m < K; ++m) {
+        Tm[m] = 0.0f;
+        if (m >= nk_warp) break;
+        if (m < nk) {
+            const float4 pay = W.bucket_pay[top.e[m]];
             const FragW w = frag_weights(F, pay.x, pay.y, pay.z, L, j, k);
-            const float dg = sc_dg[m * TP + px];
-            const float beta = w.wx * w.wy;
-            g_al += dg * beta * w.iota;
-            const float dw = dg * pay.w;
-            gx += dw * w.wy * w.iota * w.dwx;
-            gy += dw * w.wx * w.iota * w.dwy;
-            gs += dw * beta * w.diota;
+            Tm[m] = T;
+            T = T * (1.0f - w.wx * w.wy * w.iota * pay.w);
         }
-        // descriptor gradient: sum over taps of T_m gamma_m G(pixel)
-        float *gd = gdesc + (long long)i * D;
-        for (int d0 = 0; d0 < D; d0 += 4) {
-            float4 a = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            for (int q = 0; q < nt; ++q) {
-                const int px = tap_px[q];
-                const long long pix = F.pix_base[L] + (long long)(g.y0 + px / F.tile_w) * F.lw[L] +
-                                      (g.x0 + px % F.tile_w);
-                const float tg = sc_tg[tap_m[q] * TP + px];
-                const float *Gp = grad_pyr + pix * D + d0;
-                a.x += tg * __ldg(Gp);
-                if (d0 + 1 < D) a.y += tg * __ldg(Gp + 1);
-                if (d0 + 2 < D) a.z += tg * __ldg(Gp + 2);
-                if (d0 + 3 < D) a.w += tg * __ldg(Gp + 3);
-            }
-            if (F.grad_vec) {
-                atomic_add4(gd + d0, a);
-            } else {
-                atomicAdd(gd + d0, a.x);
-                if (d0 + 1 < D) atomicAdd(gd + d0 + 1, a.y);
-                if (d0 + 2 < D) atomicAdd(gd + d0 + 2, a.z);
-                if (d0 + 3 < D) atomicAdd(gd + d0 + 3, a.w);
-            }
-        }
-        atomicAdd(gop + i, g_al);
-        const float iz = 1.0f / z;
-        const float dXc = gx * F.fx * iz;
-        const float dYc = gy * F.fy * iz;
-        const float dZc = -(gx * (pay.x - F.cx) + gy * (pay.y - F.cy) + gs * pay.z) * iz;
-        atomicAdd(gsw + i, gs * F.fx * iz);
-        atomicAdd(gpos + 3 * (long long)i + 0, F.R[0] * dXc + F.R[3] * dYc + F.R[6] * dZc);
-        atomicAdd(gpos + 3 * (long long)i + 1, F.R[1] * dXc + F.R[4] * dYc + F.R[7] * dZc);
-        atomicAdd(gpos + 3 * (long long)i + 2, F.R[2] * dXc + F.R[5] * dYc + F.R[8] * dZc);
+    }
+    if (nk == 0) return;
+    float G[kMaxGradD];
+    for (int d = 0; d < D; ++d) G[d] = __ldg(grad_pyr + pix * D + d);
+    float R = 0.0f;
+#pragma unroll
+    for (int m = K - 1; m >= 0; --m) {
+        if (m >= nk) continue;
+        const unsigned long long key = top.key[m];
+        const float4 pay = W.bucket_pay[top.e[m]];
+        adjoint_fragment<DescT>(F, L, j, k, (unsigned)(key & 0xFFFFFFFFull), pay.x, pay.y,
+                                __uint_as_float((unsigned)(key >> 32)), pay.z, pay.w, Tm[m], G, R, desc, gpos, gsw,
+                                gop, gdesc);
     }
 }
 
@@ -505,17 +428,17 @@ __global__ void __launch_bounds__(kBlock) k_stored_backward(Frame F, long long P
         while (L + 1 < F.n_layers && pix >= F.pix_base[L + 1]) ++L;
         const long long local = pix - F.pix_base[L];
         const int j = (int)(local % F.lw[L]), k = (int)(local / F.lw[L]);
-        float gam[K], Tm[K];
+        float Tm[K];
         float T = 1.0f;
 #pragma unroll
         for (int m = 0; m < K; ++m) {
+            Tm[m] = 0.0f;
             if (m < nk) {
                 const unsigned i = kept[pix * K + m];
                 const float4 r = rec[i];
                 const FragW w = frag_weights(F, r.x, r.y, r.w, L, j, k);
-                gam[m] = w.wx * w.wy * w.iota * __ldg(opacity + i);
                 Tm[m] = T;
-                T = T * (1.0f - gam[m]);
+                T = T * (1.0f - w.wx * w.wy * w.iota * __ldg(opacity + i));
             }
         }
         float G[kMaxGradD];
@@ -527,8 +450,8 @@ __global__ void __launch_bounds__(kBlock) k_stored_backward(Frame F, long long P
             if (m >= nk) continue;
             const unsigned i = kept[pix * K + m];
             const float4 r = rec[i];
-            adjoint_fragment<DescT>(F, L, j, k, i, r.x, r.y, r.z, r.w, __ldg(opacity + i), gam[m], Tm[m], G, R,
-                                    desc, gpos, gsw, gop, gdesc);
+            adjoint_fragment<DescT>(F, L, j, k, i, r.x, r.y, r.z, r.w, __ldg(opacity + i), Tm[m], G, R, desc, gpos,
+                                    gsw, gop, gdesc);
         }
     }
 }
