@@ -43,7 +43,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="ground6m_1080p")
     ap.add_argument("--mode", choices=["recompute", "store"], default="recompute")
-    ap.add_argument("--tile", default="16x16")
+    ap.add_argument("--tile", default="16x8")
     ap.add_argument("--points", type=int, default=0, help="override the workload's point count (profiling)")
     ap.add_argument("--ref-sample", type=int, default=2_000_000, help="points per reference-arm step")
     ap.add_argument("--cpu-frames", type=int, default=2, help="full oracle frames timed for cpu_baseline")

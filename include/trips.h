@@ -74,7 +74,8 @@
  *   number of candidate fragments of the pixel before the K cap.
  *
  * Sizes: n < 2^27 points, 1 <= n_layers <= 16, K in {4, 8, 16, 32},
- * 1 <= D <= 64, width and height in [1, 32768], tile_w * tile_h <= 1024.
+ * 1 <= D <= 64, width and height in [1, 32768], tile_w * tile_h <= 1024 (a
+ * tile whose CTA does not fit the kernel's registers returns TP_ERR_UNSUPPORTED).
  */
 #ifndef TRIPS_H
 #define TRIPS_H
@@ -130,7 +131,7 @@ typedef struct {
     int32_t desc_dtype; /* TP_F32 or TP_BF16 */
     int32_t mode;       /* TP_STORE_LISTS or TP_RECOMPUTE (see tp_splat_backward) */
     int32_t tile_w;     /* screen tile of the binning and blend kernels, in pixels */
-    int32_t tile_h;     /*   of each layer; 0 = the default 16 x 16 */
+    int32_t tile_h;     /*   of each layer; 0 = the default 16 x 8 */
 } tp_config;
 
 /*

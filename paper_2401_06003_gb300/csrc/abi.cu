@@ -55,7 +55,7 @@ tp_status make_frame(const tp_config *cfg, const tp_camera *cam, Frame &F)
     if (cfg->K < 1 || cfg->K > 255) return TP_ERR_INVALID_ARG;
     if (cfg->K != 4 && cfg->K != 8 && cfg->K != 16 && cfg->K != 32) return TP_ERR_UNSUPPORTED;
     const int tw = cfg->tile_w > 0 ? cfg->tile_w : 16;
-    const int th = cfg->tile_h > 0 ? cfg->tile_h : 16;
+    const int th = cfg->tile_h > 0 ? cfg->tile_h : 8;
     if (tw > 64 || th > 64 || cfg->tile_w < 0 || cfg->tile_h < 0) return TP_ERR_INVALID_ARG;
     if (tw * th > 1024) return TP_ERR_UNSUPPORTED;  // one thread per tile pixel
     std::memset(&F, 0, sizeof(F));
@@ -81,13 +81,12 @@ tp_status make_frame(const tp_config *cfg, const tp_camera *cam, Frame &F)
     }
     F.tile_base[F.n_layers] = tiles;
     F.n_tiles = tiles;
-    // Tile CTAs: one thread per pixel; the chunk of tile-list entries merged at
-    // a time is sized so that a CTA's shared memory stays near 72 KB (three
-    // CTAs per SM) when the kept lists leave room for it.
+    // Tile CTAs: one thread per pixel, kept lists in registers; shared memory
+    // holds one chunk of tile-list entries' fragments (12 bytes each, at most
+    // four per entry), sized to about 40 KB per CTA.
     F.tile_px = tw * th;
     F.tile_threads = (F.tile_px + 31) / 32 * 32;
-    const int64_t kept_bytes = (int64_t)F.tile_px * F.K * 12;
-    const int64_t avail = 72 * 1024 - kept_bytes - (3 * F.tile_threads + 32) * 4;
+    const int64_t avail = 40 * 1024 - (3 * F.tile_threads + 32) * 4;
     int64_t chunk = avail / 48;
     if (chunk < 128) chunk = 128;
     if (chunk > 2048) chunk = 2048;
@@ -157,7 +156,12 @@ tp_status common_checks(const tp_config *cfg, const tp_camera *cam, int64_t n, v
     return bind_workspace(F, ws, ws_bytes, W);
 }
 
-tp_status from_cuda(cudaError_t e) { return e == cudaSuccess ? TP_OK : TP_ERR_CUDA; }
+tp_status from_cuda(cudaError_t e)
+{
+    if (e == cudaSuccess) return TP_OK;
+    if (e == cudaErrorInvalidConfiguration) return TP_ERR_UNSUPPORTED;  // tile too large for the kernel
+    return TP_ERR_CUDA;
+}
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 

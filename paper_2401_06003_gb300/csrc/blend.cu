@@ -460,11 +460,17 @@ __global__ void __launch_bounds__(kBlock) k_stored_backward(Frame F, long long P
 // Launchers
 // ---------------------------------------------------------------------------
 
+// Raises the kernel's dynamic shared memory limit when needed and checks that
+// a CTA of `threads` threads fits the kernel's register use.
 template <class KernelT>
-static cudaError_t allow_smem(KernelT kernel, size_t bytes)
+static cudaError_t prepare_tile_kernel(KernelT kernel, size_t smem_bytes, int threads)
 {
-    if (bytes <= 48 * 1024) return cudaSuccess;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaFuncAttributes attr;
+    cudaError_t e = cudaFuncGetAttributes(&attr, kernel);
+    if (e != cudaSuccess) return e;
+    if (threads > attr.maxThreadsPerBlock) return cudaErrorInvalidConfiguration;
+    if (smem_bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
 }
 
 template <int K, typename DescT>
@@ -472,7 +478,7 @@ static cudaError_t blend_impl(const Frame &F, const Workspace &W, const void *de
                               unsigned char *n_kept, float *t_final, unsigned *n_frag, cudaStream_t stream)
 {
     const size_t smem = tile_smem_bytes(F, false);
-    cudaError_t e = allow_smem(k_tile_blend<K, DescT>, smem);
+    cudaError_t e = prepare_tile_kernel(k_tile_blend<K, DescT>, smem, F.tile_threads);
     if (e != cudaSuccess) return e;
     k_tile_blend<K, DescT><<<F.n_tiles, F.tile_threads, smem, stream>>>(
         F, W, static_cast<const DescT *>(desc), pyramid, kept, n_kept, t_final, n_frag);
@@ -496,7 +502,7 @@ static cudaError_t backward_impl(const Frame &F, const Workspace &W, const float
         return cudaGetLastError();
     }
     const size_t smem = tile_smem_bytes(F, true);
-    cudaError_t e = allow_smem(k_tile_backward<K, DescT>, smem);
+    cudaError_t e = prepare_tile_kernel(k_tile_backward<K, DescT>, smem, F.tile_threads);
     if (e != cudaSuccess) return e;
     k_tile_backward<K, DescT><<<F.n_tiles, F.tile_threads, smem, stream>>>(F, W, d, grad_pyr, gpos, gsw, gop,
                                                                            gdesc);

@@ -53,7 +53,7 @@ class Renderer:
     """
 
     def __init__(self, camera, n_layers: int, K: int = 16, D: int = 4, eps: float = 0.25,
-                 desc_dtype=torch.float32, mode: str = "recompute", tile=(16, 16), device=None):
+                 desc_dtype=torch.float32, mode: str = "recompute", tile=(16, 8), device=None):
         self.lib = _lib.load()
         self.camera = camera
         self.cam = _lib.make_camera(camera)

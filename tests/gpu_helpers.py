@@ -24,7 +24,7 @@ def to_dev(a, dtype=torch.float32):
     return torch.as_tensor(np.ascontiguousarray(a)).to(device=device(), dtype=dtype).contiguous()
 
 
-def gpu_frame(scene, view=0, K=None, mode="store", tile=(16, 16), desc_dtype=torch.float32, desc=None,
+def gpu_frame(scene, view=0, K=None, mode="store", tile=(16, 8), desc_dtype=torch.float32, desc=None,
               capacity=0, pos=None, expect_flags=0):
     """Render one view on the GPU with every optional output; numpy results.
 

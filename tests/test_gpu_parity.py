@@ -74,7 +74,7 @@ def test_hand_examples_on_gpu(golden_dir):
             assert out["n_frag"].sum() == len(ex["fragments"])
 
 
-@pytest.mark.parametrize("tile", [(16, 16), (32, 8), (8, 8), (13, 7)])
+@pytest.mark.parametrize("tile", [(16, 8), (16, 16), (32, 8), (8, 8), (13, 7)])
 @pytest.mark.parametrize("K", [4, 8, 16, 32])
 def test_ragged_image_tiles_and_caps(tile, K):
     sc = scenes.scene_uniform_cube(n=4000, seed=5, res=64)
@@ -86,6 +86,14 @@ def test_ragged_image_tiles_and_caps(tile, K):
     ofr = _oracle(sc)
     compare_records(out["records"], ofr)
     compare_forward(out, ofr.render(), r.layer_offsets, name=f"tile{tile} K{K}")
+
+
+def test_oversized_tile_is_rejected(cube):
+    """A tile whose CTA does not fit the kernel's registers is refused, not launched."""
+    from paper_2401_06003_gb300 import TripsError
+    with pytest.raises(TripsError) as exc:
+        gpu_frame(cube, tile=(32, 32), mode="recompute")
+    assert exc.value.status in (6,)
 
 
 def test_dense_pixel_cap_and_ties():
