@@ -90,6 +90,9 @@ tp_status make_frame(const tp_config *cfg, const tp_camera *cam, Frame &F)
     int64_t chunk = avail / 48;
     if (chunk < 128) chunk = 128;
     if (chunk > 2048) chunk = 2048;
+    // after the build the backward keeps each pixel's list (16 bytes a slot) there
+    const int64_t need = ((int64_t)16 * F.K * F.tile_px + 47) / 48;
+    if (chunk < need) chunk = need;
     F.chunk = (int)chunk;
     if (tpk::tile_smem_bytes(F, true) > kMaxTileSmem) return TP_ERR_UNSUPPORTED;
     return TP_OK;

@@ -360,7 +360,9 @@ __device__ __forceinline__ void adjoint_fragment(const Frame &F, int L, int j, i
 }
 
 // Backward with the lists rebuilt from the workspace's tile lists: each
-// pixel thread runs the adjoint of its own blend back to front.
+// pixel thread runs the adjoint of its own blend back to front.  After the
+// build, the thread's kept list moves from registers to its private slots in
+// the (now idle) chunk area, so the adjoint is one rolled loop.
 template <int K, typename DescT>
 __global__ void k_tile_backward(Frame F, Workspace W, const DescT *__restrict__ desc,
                                 const float *__restrict__ grad_pyr, float *__restrict__ gpos, float *__restrict__ gsw,
@@ -372,39 +374,36 @@ __global__ void k_tile_backward(Frame F, Workspace W, const DescT *__restrict__ 
     const TileGeom g = tile_geom(F, tile);
     TopK<K> top;
     unsigned nfr;
-    int nk = build_topk<K>(F, W, tile, g, S, top, &nfr);
+    const int nk = build_topk<K>(F, W, tile, g, S, top, &nfr);
     const int TP = F.tile_px, tid = threadIdx.x, L = g.L, D = F.D;
     const int j = g.x0 + tid % F.tile_w, k = g.y0 + tid / F.tile_w;
-    const bool active = tid < TP && j < F.lw[L] && k < F.lh[L];
-    if (!active) nk = 0;
-    const int nk_warp = __reduce_max_sync(0xffffffffu, nk);
-    if (nk_warp == 0) return;
-    const long long pix = F.pix_base[L] + (long long)k * F.lw[L] + j;
-    float Tm[K];
-    float T = 1.0f;
+    if (!(tid < TP && j < F.lw[L] && k < F.lh[L]) || nk == 0) return;
+    // private slot-major copies: key [K][TP], entry [K][TP], T_m [K][TP]
+    unsigned long long *kk = S.ck;
+    unsigned *ke = reinterpret_cast<unsigned *>(S.ck + (size_t)K * TP);
+    float *kt = reinterpret_cast<float *>(ke + (size_t)K * TP);
 #pragma unroll
     for (int m = 0; m < K; ++m) {
-        Tm[m] = 0.0f;
-        if (m >= nk_warp) break;
-        if (m < nk) {
-            const float4 pay = W.bucket_pay[top.e[m]];
-            const FragW w = frag_weights(F, pay.x, pay.y, pay.z, L, j, k);
-            Tm[m] = T;
-            T = T * (1.0f - w.wx * w.wy * w.iota * pay.w);
-        }
+        kk[m * TP + tid] = top.key[m];
+        ke[m * TP + tid] = top.e[m];
     }
-    if (nk == 0) return;
+    float T = 1.0f;
+    for (int m = 0; m < nk; ++m) {
+        const float4 pay = W.bucket_pay[ke[m * TP + tid]];
+        const FragW w = frag_weights(F, pay.x, pay.y, pay.z, L, j, k);
+        kt[m * TP + tid] = T;
+        T = T * (1.0f - w.wx * w.wy * w.iota * pay.w);
+    }
+    const long long pix = F.pix_base[L] + (long long)k * F.lw[L] + j;
     float G[kMaxGradD];
     for (int d = 0; d < D; ++d) G[d] = __ldg(grad_pyr + pix * D + d);
     float R = 0.0f;
-#pragma unroll
-    for (int m = K - 1; m >= 0; --m) {
-        if (m >= nk) continue;
-        const unsigned long long key = top.key[m];
-        const float4 pay = W.bucket_pay[top.e[m]];
+    for (int m = nk - 1; m >= 0; --m) {
+        const unsigned long long key = kk[m * TP + tid];
+        const float4 pay = W.bucket_pay[ke[m * TP + tid]];
         adjoint_fragment<DescT>(F, L, j, k, (unsigned)(key & 0xFFFFFFFFull), pay.x, pay.y,
-                                __uint_as_float((unsigned)(key >> 32)), pay.z, pay.w, Tm[m], G, R, desc, gpos, gsw,
-                                gop, gdesc);
+                                __uint_as_float((unsigned)(key >> 32)), pay.z, pay.w, kt[m * TP + tid], G, R, desc,
+                                gpos, gsw, gop, gdesc);
     }
 }
 
