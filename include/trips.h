@@ -182,6 +182,8 @@ TP_API tp_status tp_splat_forward(const tp_config *cfg, const tp_camera *cam, in
  *   C = sum_m T_m gamma_m tau_m,  T_m = prod_{i<m} (1 - gamma_i),
  *   gamma = beta iota alpha (Eq. 3).
  * The fragments come from the workspace's tile lists (tp_splat_forward).
+ * The call also leaves each pixel's largest kept key in the workspace, for a
+ * TP_RECOMPUTE backward pass.
  *   desc [n][D] (device, read)
  *   pyramid [P][D] (device, written; every pixel)
  *   kept [P][K], n_kept [P], t_final [P], n_frag [P] (device, written;
@@ -200,8 +202,9 @@ TP_API tp_status tp_blend(const tp_config *cfg, const tp_camera *cam, int64_t n,
  * (device float32, overwritten; every entry, zero where a point has no kept
  * fragment).  With kept and n_kept (TP_STORE_LISTS) the per-pixel lists come
  * from tp_blend.  With kept == NULL (TP_RECOMPUTE) the lists are rebuilt from
- * the workspace's tile lists, which must still hold this frame's
- * tp_splat_forward result.  The adjoint of one pixel runs back to front:
+ * the workspace's tile lists and the per-pixel largest kept key that
+ * tp_blend leaves in the workspace (8 bytes per pixel); the workspace must
+ * still hold this frame's tp_splat_forward and tp_blend results.  The adjoint of one pixel runs back to front:
  *   R_M = 0,  dL/dgamma_m = T_m (G.tau_m - R_m),
  *   R_{m-1} = gamma_m G.tau_m + (1 - gamma_m) R_m,  dL/dtau_m = T_m gamma_m G,
  * and chains through gamma = beta iota alpha to alpha, the screen position

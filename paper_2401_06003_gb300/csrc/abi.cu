@@ -98,12 +98,13 @@ tp_status make_frame(const tp_config *cfg, const tp_camera *cam, Frame &F)
     return TP_OK;
 }
 
-// Workspace: status word, tile counts, tile offsets, fill cursors, then the
-// tile lists as two arrays: 8-byte fragment keys and 16-byte payloads.
+// Workspace: status word, tile counts, tile offsets, fill cursors, the
+// per-pixel largest kept keys, then the tile lists as two arrays: 8-byte
+// fragment keys and 16-byte payloads.
 constexpr int64_t kEntryBytes = 24;
 
 struct WsLayout {
-    int64_t count, off, cursor, key, pay, end;
+    int64_t count, off, cursor, kmax, key, pay, end;
 };
 
 WsLayout layout_for(const Frame &F, int64_t capacity)
@@ -113,7 +114,8 @@ WsLayout layout_for(const Frame &F, int64_t capacity)
     w.count = kAlign;
     w.off = align_up(w.count + 4 * T * tpk::kCopies);
     w.cursor = align_up(w.off + 4 * (T + 1));
-    w.key = align_up(w.cursor + 4 * T * tpk::kCopies);
+    w.kmax = align_up(w.cursor + 4 * T * tpk::kCopies);
+    w.key = align_up(w.kmax + 8 * (int64_t)F.pix_base[F.n_layers]);
     w.pay = align_up(w.key + 8 * capacity);
     w.end = w.pay + 16 * capacity;
     return w;
@@ -144,6 +146,7 @@ tp_status bind_workspace(const Frame &F, void *ws, int64_t ws_bytes, Workspace &
     W.tile_count = reinterpret_cast<unsigned *>(base + w.count);
     W.tile_off = reinterpret_cast<unsigned *>(base + w.off);
     W.tile_cursor = reinterpret_cast<unsigned *>(base + w.cursor);
+    W.kmax = reinterpret_cast<unsigned long long *>(base + w.kmax);
     W.bucket_key = reinterpret_cast<unsigned long long *>(base + w.key);
     W.bucket_pay = reinterpret_cast<float4 *>(base + w.pay);
     W.capacity = (unsigned)cap;

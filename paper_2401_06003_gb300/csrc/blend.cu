@@ -295,6 +295,12 @@ __global__ void k_tile_blend(Frame F, Workspace W, const DescT *__restrict__ des
         }
     }
     if (!active) return;
+    // the largest kept key: the backward's rebuild keeps exactly the keys <= it
+    unsigned long long kmax = 0ull;
+#pragma unroll
+    for (int m = 0; m < K; ++m)
+        if (m == nk - 1) kmax = top.key[m];
+    W.kmax[pix] = kmax;
     if (kept) {
 #pragma unroll
         for (int m = 0; m < K; ++m)
@@ -359,10 +365,12 @@ __device__ __forceinline__ void adjoint_fragment(const Frame &F, int L, int j, i
     atomicAdd(gpos + 3 * (long long)i + 2, F.R[2] * dXc + F.R[5] * dYc + F.R[8] * dZc);
 }
 
-// Backward with the lists rebuilt from the workspace's tile lists: each
-// pixel thread runs the adjoint of its own blend back to front.  After the
-// build, the thread's kept list moves from registers to its private slots in
-// the (now idle) chunk area, so the adjoint is one rolled loop.
+// Backward with the lists rebuilt from the workspace's tile lists.  The blend
+// left each pixel's largest kept key; a fragment is kept exactly when its key
+// is not larger, so one pass over the tile's entries drops every kept
+// fragment into one of its pixel's K slots (no selection work), each pixel's
+// thread sorts its at most K slots, and runs the adjoint of its blend back to
+// front in a rolled loop.
 template <int K, typename DescT>
 __global__ void k_tile_backward(Frame F, Workspace W, const DescT *__restrict__ desc,
                                 const float *__restrict__ grad_pyr, float *__restrict__ gpos, float *__restrict__ gsw,
@@ -372,16 +380,43 @@ __global__ void k_tile_backward(Frame F, Workspace W, const DescT *__restrict__ 
     const TileSmem S = carve(F, smem_raw);
     const int tile = blockIdx.x;
     const TileGeom g = tile_geom(F, tile);
-    TopK<K> top;
-    unsigned nfr;
-    const int nk = build_topk<K>(F, W, tile, g, S, top, &nfr);
-    const int TP = F.tile_px, tid = threadIdx.x, L = g.L, D = F.D;
+    const int TP = F.tile_px, tid = threadIdx.x, NT = blockDim.x, L = g.L, D = F.D;
     const int j = g.x0 + tid % F.tile_w, k = g.y0 + tid / F.tile_w;
-    if (!(tid < TP && j < F.lw[L] && k < F.lh[L]) || nk == 0) return;
-    // private slot-major copies: key [K][TP], entry [K][TP], T_m [K][TP]
+    const bool active = tid < TP && j < F.lw[L] && k < F.lh[L];
+    const long long pix = F.pix_base[L] + (long long)k * F.lw[L] + j;
+    // slot-major private slots in the chunk area: key [K][TP], entry [K][TP], T_m [K][TP]
     unsigned long long *kk = S.ck;
     unsigned *ke = reinterpret_cast<unsigned *>(S.ck + (size_t)K * TP);
     float *kt = reinterpret_cast<float *>(ke + (size_t)K * TP);
+    unsigned long long *thr = reinterpret_cast<unsigned long long *>(S.off);  // [TP] (off, cur are 8-aligned pairs)
+    S.cnt[tid] = 0u;
+    if (tid < TP) thr[tid] = active ? W.kmax[pix] : 0ull;
+    __syncthreads();
+    unsigned end = W.tile_off[tile + 1];
+    if (end > W.capacity) end = W.capacity;
+    unsigned beg = W.tile_off[tile];
+    if (beg > end) beg = end;
+    for (unsigned e = beg + tid; e < end; e += NT) {
+        const unsigned long long key = W.bucket_key[e];
+        entry_taps(F, g, W.bucket_pay[e], [&](int px) {
+            if (key <= thr[px]) {
+                const unsigned q = atomicAdd(S.cnt + px, 1u);
+                if (q < (unsigned)K) {
+                    kk[q * TP + px] = key;
+                    ke[q * TP + px] = e;
+                }
+            }
+        });
+    }
+    __syncthreads();
+    if (!active) return;
+    int nk = (int)S.cnt[tid];
+    if (nk > K) nk = K;
+    if (nk == 0) return;
+    // sort the pixel's slots (at most K) by key
+    TopK<K> top;
+    top.clear();
+    for (int q = 0; q < nk; ++q) top.insert(kk[q * TP + tid], ke[q * TP + tid]);
 #pragma unroll
     for (int m = 0; m < K; ++m) {
         kk[m * TP + tid] = top.key[m];
@@ -394,7 +429,6 @@ __global__ void k_tile_backward(Frame F, Workspace W, const DescT *__restrict__ 
         kt[m * TP + tid] = T;
         T = T * (1.0f - w.wx * w.wy * w.iota * pay.w);
     }
-    const long long pix = F.pix_base[L] + (long long)k * F.lw[L] + j;
     float G[kMaxGradD];
     for (int d = 0; d < D; ++d) G[d] = __ldg(grad_pyr + pix * D + d);
     float R = 0.0f;

@@ -55,6 +55,7 @@ struct Workspace {
     unsigned *tile_cursor;  // [n_tiles][kCopies] fill cursor of each copy (relative to tile_off)
     unsigned long long *bucket_key;  // [capacity] fragment key (z bits, point index) of each entry
     float4 *bucket_pay;     // [capacity] (x, y, s, alpha) of the entry's point
+    unsigned long long *kmax;  // [P] largest kept key of each pixel (0: none), written by the blend
     unsigned capacity;
 };
 
