@@ -255,6 +255,13 @@ __global__ void k_tile_blend(Frame F, Workspace W, const DescT *__restrict__ des
     if (!active) nk = 0;
     const int nk_warp = __reduce_max_sync(0xffffffffu, nk);
     const long long pix = F.pix_base[L] + (long long)k * F.lw[L] + j;
+    if (active) {
+        // the largest kept key: the backward's rebuild keeps exactly the keys <= it
+        unsigned long long kmax = 0ull;
+#pragma unroll
+        for (int m = 0; m < K; ++m) kmax = top.key[m] != kEmptyKey && top.key[m] > kmax ? top.key[m] : kmax;
+        W.kmax[pix] = kmax;
+    }
     // front to back: weights T_m gamma_m (Eq. 6-7)
     float wgt[K];
     float T = 1.0f;
@@ -295,12 +302,6 @@ __global__ void k_tile_blend(Frame F, Workspace W, const DescT *__restrict__ des
         }
     }
     if (!active) return;
-    // the largest kept key: the backward's rebuild keeps exactly the keys <= it
-    unsigned long long kmax = 0ull;
-#pragma unroll
-    for (int m = 0; m < K; ++m)
-        if (m == nk - 1) kmax = top.key[m];
-    W.kmax[pix] = kmax;
     if (kept) {
 #pragma unroll
         for (int m = 0; m < K; ++m)
