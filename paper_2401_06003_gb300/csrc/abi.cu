@@ -139,7 +139,7 @@ tp_status bind_workspace(const Frame &F, void *ws, int64_t ws_bytes, Workspace &
 {
     if (!ws || ((uintptr_t)ws % kAlign) != 0) return TP_ERR_INVALID_ARG;
     const int64_t cap = capacity_for(F, ws_bytes);
-    if (cap < 0) return TP_ERR_INVALID_ARG;
+    if (cap < 1) return TP_ERR_INVALID_ARG;
     const WsLayout w = layout_for(F, cap);
     char *base = static_cast<char *>(ws);
     W.status = reinterpret_cast<unsigned *>(base);

@@ -121,11 +121,14 @@ __device__ __forceinline__ void entry_taps(const Frame &F, const TileGeom &g, co
 // with the workspace entry of each; empty slots hold kEmptyKey.
 template <int K>
 struct TopK {
+    static_assert(K % 4 == 0, "K must be a multiple of 4");
     unsigned long long key[K];
     unsigned e[K];
+    int n;  // valid slots
 
     __device__ __forceinline__ void clear()
     {
+        n = 0;
 #pragma unroll
         for (int m = 0; m < K; ++m) {
             key[m] = kEmptyKey;
@@ -135,11 +138,13 @@ struct TopK {
 
     // Compare-exchange chain: after slot m, slots 0..m hold the m+1 smallest
     // of (old slots 0..m, new key) in order; the largest key falls off the end.
+    // Slots past the n valid ones are empty, so the chain stops at slot n.
     __device__ __forceinline__ void insert(unsigned long long k, unsigned ee)
     {
         if (k >= key[K - 1]) return;
 #pragma unroll
         for (int m = 0; m < K; ++m) {
+            if (m > n) break;
             const bool lt = k < key[m];
             const unsigned long long tk = key[m];
             const unsigned te = e[m];
@@ -148,6 +153,7 @@ struct TopK {
             k = lt ? tk : k;
             ee = lt ? te : ee;
         }
+        n = n < K ? n + 1 : K;
     }
 };
 
@@ -262,33 +268,49 @@ __global__ void k_tile_blend(Frame F, Workspace W, const DescT *__restrict__ des
         for (int m = 0; m < K; ++m) kmax = top.key[m] != kEmptyKey && top.key[m] > kmax ? top.key[m] : kmax;
         W.kmax[pix] = kmax;
     }
-    // front to back: weights T_m gamma_m (Eq. 6-7)
+    // front to back: weights T_m gamma_m (Eq. 6-7).  Loads go out four
+    // slots at a time, ahead of the dependent arithmetic; unused slots hold
+    // entry 0 and descriptor row 0, valid addresses whose values are ignored.
+    constexpr int B = 4;
     float wgt[K];
     float T = 1.0f;
 #pragma unroll
-    for (int m = 0; m < K; ++m) {
-        wgt[m] = 0.0f;
-        if (m >= nk_warp) break;
-        if (m < nk) {
-            const float4 pay = W.bucket_pay[top.e[m]];
-            const FragW w = frag_weights(F, pay.x, pay.y, pay.z, L, j, k);
-            const float gam = w.wx * w.wy * w.iota * pay.w;
-            wgt[m] = T * gam;
-            T = T * (1.0f - gam);
+    for (int m0 = 0; m0 < K; m0 += B) {
+        if (m0 >= nk_warp) break;
+        float4 pay[B];
+#pragma unroll
+        for (int u = 0; u < B; ++u) pay[u] = W.bucket_pay[top.e[m0 + u]];
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            const int m = m0 + u;
+            wgt[m] = 0.0f;
+            if (m < nk) {
+                const FragW w = frag_weights(F, pay[u].x, pay[u].y, pay[u].z, L, j, k);
+                const float gam = w.wx * w.wy * w.iota * pay[u].w;
+                wgt[m] = T * gam;
+                T = T * (1.0f - gam);
+            }
         }
     }
     const int D = F.D;
     for (int d0 = 0; d0 < D; d0 += 4) {
         float4 c = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll
-        for (int m = 0; m < K; ++m) {
-            if (m >= nk_warp) break;
-            if (m < nk) {
-                const float4 t = load_desc4(desc, (unsigned)(top.key[m] & 0xFFFFFFFFull), D, d0, F.desc_vec);
-                c.x += wgt[m] * t.x;
-                c.y += wgt[m] * t.y;
-                c.z += wgt[m] * t.z;
-                c.w += wgt[m] * t.w;
+        for (int m0 = 0; m0 < K; m0 += B) {
+            if (m0 >= nk_warp) break;
+            float4 t[B];
+#pragma unroll
+            for (int u = 0; u < B; ++u)
+                t[u] = load_desc4(desc, m0 + u < nk ? (unsigned)(top.key[m0 + u] & 0xFFFFFFFFull) : 0u, D, d0,
+                                  F.desc_vec);
+#pragma unroll
+            for (int u = 0; u < B; ++u) {
+                if (m0 + u < nk) {
+                    c.x += wgt[m0 + u] * t[u].x;
+                    c.y += wgt[m0 + u] * t[u].y;
+                    c.z += wgt[m0 + u] * t[u].z;
+                    c.w += wgt[m0 + u] * t[u].w;
+                }
             }
         }
         if (active) {
@@ -322,10 +344,11 @@ __device__ __forceinline__ void atomic_add4(float *p, float4 v)
 
 // Adjoint of one kept fragment, given its forward quantities; scatters the
 // point gradients.  G is the pixel's dL/dC; R the running back-to-front term.
+// t0 holds channels [0, 4) of the point's descriptor, loaded by the caller.
 template <typename DescT>
 __device__ __forceinline__ void adjoint_fragment(const Frame &F, int L, int j, int k, unsigned i, float x, float y,
                                                  float z, float s, float al, float Tm, const float *G, float &R,
-                                                 const DescT *__restrict__ desc, float *__restrict__ gpos,
+                                                 float4 t0, const DescT *__restrict__ desc, float *__restrict__ gpos,
                                                  float *__restrict__ gsw, float *__restrict__ gop,
                                                  float *__restrict__ gdesc)
 {
@@ -335,7 +358,7 @@ __device__ __forceinline__ void adjoint_fragment(const Frame &F, int L, int j, i
     const float gam = beta * w.iota * al;
     float gdot = 0.0f;
     for (int d0 = 0; d0 < D; d0 += 4) {
-        const float4 t = load_desc4(desc, i, D, d0, F.desc_vec);
+        const float4 t = d0 == 0 ? t0 : load_desc4(desc, i, D, d0, F.desc_vec);
         gdot += G[d0] * t.x;
         if (d0 + 1 < D) gdot += G[d0 + 1] * t.y;
         if (d0 + 2 < D) gdot += G[d0 + 2] * t.z;
@@ -432,13 +455,27 @@ __global__ void k_tile_backward(Frame F, Workspace W, const DescT *__restrict__ 
     }
     float G[kMaxGradD];
     for (int d = 0; d < D; ++d) G[d] = __ldg(grad_pyr + pix * D + d);
+    // back to front, four slots at a time: the loads of a batch go out first
     float R = 0.0f;
-    for (int m = nk - 1; m >= 0; --m) {
-        const unsigned long long key = kk[m * TP + tid];
-        const float4 pay = W.bucket_pay[ke[m * TP + tid]];
-        adjoint_fragment<DescT>(F, L, j, k, (unsigned)(key & 0xFFFFFFFFull), pay.x, pay.y,
-                                __uint_as_float((unsigned)(key >> 32)), pay.z, pay.w, kt[m * TP + tid], G, R, desc,
-                                gpos, gsw, gop, gdesc);
+    constexpr int B = 4;
+    for (int m1 = nk - 1; m1 >= 0; m1 -= B) {
+        unsigned long long key[B];
+        float4 pay[B], t0[B];
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            const int m = m1 - u >= 0 ? m1 - u : 0;
+            key[u] = kk[m * TP + tid];
+            pay[u] = W.bucket_pay[ke[m * TP + tid]];
+            t0[u] = load_desc4(desc, (unsigned)(key[u] & 0xFFFFFFFFull), D, 0, F.desc_vec);
+        }
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            const int m = m1 - u;
+            if (m < 0) break;
+            adjoint_fragment<DescT>(F, L, j, k, (unsigned)(key[u] & 0xFFFFFFFFull), pay[u].x, pay[u].y,
+                                    __uint_as_float((unsigned)(key[u] >> 32)), pay[u].z, pay[u].w, kt[m * TP + tid],
+                                    G, R, t0[u], desc, gpos, gsw, gop, gdesc);
+        }
     }
 }
 
@@ -484,8 +521,8 @@ __global__ void __launch_bounds__(kBlock) k_stored_backward(Frame F, long long P
             if (m >= nk) continue;
             const unsigned i = kept[pix * K + m];
             const float4 r = rec[i];
-            adjoint_fragment<DescT>(F, L, j, k, i, r.x, r.y, r.z, r.w, __ldg(opacity + i), Tm[m], G, R, desc, gpos,
-                                    gsw, gop, gdesc);
+            adjoint_fragment<DescT>(F, L, j, k, i, r.x, r.y, r.z, r.w, __ldg(opacity + i), Tm[m], G, R,
+                                    load_desc4(desc, i, F.D, 0, F.desc_vec), desc, gpos, gsw, gop, gdesc);
         }
     }
 }
