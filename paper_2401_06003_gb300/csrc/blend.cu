@@ -138,8 +138,26 @@ struct TopK {
 
     // Compare-exchange chain: after slot m, slots 0..m hold the m+1 smallest
     // of (old slots 0..m, new key) in order; the largest key falls off the end.
-    // Slots past the n valid ones are empty, so the chain stops at slot n.
+    // Straight-line code: cheapest when lists are long (the forward build).
     __device__ __forceinline__ void insert(unsigned long long k, unsigned ee)
+    {
+        if (k >= key[K - 1]) return;
+#pragma unroll
+        for (int m = 0; m < K; ++m) {
+            const bool lt = k < key[m];
+            const unsigned long long tk = key[m];
+            const unsigned te = e[m];
+            key[m] = lt ? k : tk;
+            e[m] = lt ? ee : te;
+            k = lt ? tk : k;
+            ee = lt ? te : ee;
+        }
+        n = n < K ? n + 1 : K;
+    }
+
+    // The same chain stopped at slot n: slots past the n valid ones are empty.
+    // Cheaper when lists are short (sorting the backward's kept slots).
+    __device__ __forceinline__ void insert_short(unsigned long long k, unsigned ee)
     {
         if (k >= key[K - 1]) return;
 #pragma unroll
@@ -174,6 +192,48 @@ __device__ int build_topk(const Frame &F, const Workspace &W, int tile, const Ti
     if (beg > end) beg = end;
     unsigned nfr = 0;
     __syncthreads();
+    if (end - beg <= (unsigned)NT && end - beg <= 2u * (unsigned)F.chunk) {
+        // Small list: stage one entry per thread (key, entry, tap footprint),
+        // then every pixel thread scans the staged entries (broadcast reads)
+        // and inserts the ones that cover it.  One barrier, no atomics.
+        const unsigned E = end - beg;
+        unsigned long long *sk = S.ck;
+        unsigned *se = S.ce;
+        unsigned *sm = S.ce + 2 * F.chunk;
+        if ((unsigned)tid < E) {
+            const unsigned e = beg + tid;
+            const float4 pay = W.bucket_pay[e];
+            unsigned foot = 0u;
+            float iota, diota;
+            if (layer_weight(pay.z, g.L, F.n_layers, F.eps, iota, diota)) {
+                const AxisTaps ax = axis_taps(pay.x, g.L, F.lw[g.L]);
+                const AxisTaps ay = axis_taps(pay.y, g.L, F.lh[g.L]);
+                const int dx0 = ax.j0 - g.x0, dy0 = ay.j0 - g.y0;
+                if (dx0 >= -1 && dx0 < F.tile_w && dy0 >= -1 && dy0 < F.tile_h) {
+                    const unsigned xm = (ax.t0 ? 1u : 0u) | (ax.t1 ? 2u : 0u);
+                    const unsigned ym = (ay.t0 ? 1u : 0u) | (ay.t1 ? 2u : 0u);
+                    foot = (unsigned)(dx0 + 1) | ((unsigned)(dy0 + 1) << 7) | (xm << 14) | (ym << 16);
+                }
+            }
+            sk[tid] = W.bucket_key[e];
+            se[tid] = e;
+            sm[tid] = foot;
+        }
+        __syncthreads();
+        if (owner) {
+            const int tx = tid % F.tile_w, ty = tid / F.tile_w;
+            for (unsigned q = 0; q < E; ++q) {
+                const unsigned v = sm[q];
+                const int dx = tx - ((int)(v & 127u) - 1), dy = ty - ((int)((v >> 7) & 127u) - 1);
+                if ((unsigned)dx < 2u && (unsigned)dy < 2u && ((v >> (14 + dx)) & 1u) && ((v >> (16 + dy)) & 1u)) {
+                    top.insert(sk[q], se[q]);
+                    ++nfr;
+                }
+            }
+        }
+        *nfrag = nfr;
+        return nfr < (unsigned)K ? (int)nfr : K;
+    }
     for (unsigned c0 = beg; c0 < end; c0 += (unsigned)F.chunk) {
         const unsigned c1 = min(end, c0 + (unsigned)F.chunk);
         for (unsigned e = c0 + tid; e < c1; e += NT)
@@ -440,7 +500,7 @@ __global__ void k_tile_backward(Frame F, Workspace W, const DescT *__restrict__ 
     // sort the pixel's slots (at most K) by key
     TopK<K> top;
     top.clear();
-    for (int q = 0; q < nk; ++q) top.insert(kk[q * TP + tid], ke[q * TP + tid]);
+    for (int q = 0; q < nk; ++q) top.insert_short(kk[q * TP + tid], ke[q * TP + tid]);
 #pragma unroll
     for (int m = 0; m < K; ++m) {
         kk[m * TP + tid] = top.key[m];
