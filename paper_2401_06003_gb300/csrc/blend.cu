@@ -39,23 +39,39 @@ __device__ __forceinline__ TileGeom tile_geom(const Frame &F, int tile)
 }
 
 // Shared-memory layout of a tile CTA (16-byte aligned pieces): the current
-// chunk's fragments grouped by pixel, and the per-pixel counters.
+// chunk's fragments grouped by pixel, the chunk's tile-list entries staged
+// from global memory, and the per-pixel counters.  The fragment and staging
+// areas are contiguous (the backward reuses them as one region).
 struct TileSmem {
     unsigned long long *ck;      // [4 chunk] chunk fragment keys, grouped by pixel
-    unsigned *ce;                // [4 chunk] chunk fragment entries
+    unsigned *ce;                // [4 chunk] chunk fragment payloads
+    unsigned long long *sk;      // [chunk]   staged entry keys
+    float4 *sp;                  // [chunk]   staged entry payloads
     unsigned *cnt, *off, *cur;   // [tile_threads]
     unsigned *wsum;              // [32]
 };
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
+// Byte offsets of the pieces of the contiguous fragment + staging region;
+// every piece starts on a 16-byte boundary whatever the chunk size.
+__host__ __device__ inline size_t off_ce(size_t C) { return align16(32 * C); }
+__host__ __device__ inline size_t off_sk(size_t C) { return align16(off_ce(C) + 16 * C); }
+__host__ __device__ inline size_t off_sp(size_t C) { return align16(off_sk(C) + 8 * C); }
+__host__ __device__ inline size_t tile_region_bytes(const Frame &F)
+{
+    return align16(off_sp(F.chunk) + 16 * (size_t)F.chunk);
+}
+
 __device__ __forceinline__ TileSmem carve(const Frame &F, unsigned char *base)
 {
     TileSmem m;
-    const size_t NT = F.tile_threads;
+    const size_t NT = F.tile_threads, C = F.chunk;
     m.ck = reinterpret_cast<unsigned long long *>(base);
-    m.ce = reinterpret_cast<unsigned *>(base + (size_t)4 * F.chunk * sizeof(unsigned long long));
-    m.cnt = reinterpret_cast<unsigned *>(base + align16((size_t)4 * F.chunk * 12));
+    m.ce = reinterpret_cast<unsigned *>(base + off_ce(C));
+    m.sk = reinterpret_cast<unsigned long long *>(base + off_sk(C));
+    m.sp = reinterpret_cast<float4 *>(base + off_sp(C));
+    m.cnt = reinterpret_cast<unsigned *>(base + tile_region_bytes(F));
     m.off = m.cnt + NT;
     m.cur = m.off + NT;
     m.wsum = m.cur + NT;
@@ -65,7 +81,7 @@ __device__ __forceinline__ TileSmem carve(const Frame &F, unsigned char *base)
 size_t tile_smem_bytes(const Frame &F, bool backward)
 {
     (void)backward;
-    return align16((size_t)4 * F.chunk * 12) + (3 * (size_t)F.tile_threads + 32) * sizeof(unsigned);
+    return tile_region_bytes(F) + (3 * (size_t)F.tile_threads + 32) * sizeof(unsigned);
 }
 
 // Exclusive scan of v over the CTA (blockDim.x <= 1024, a multiple of 32).
@@ -117,8 +133,37 @@ __device__ __forceinline__ void entry_taps(const Frame &F, const TileGeom &g, co
     }
 }
 
+// Like entry_taps, also passing each tap's fragment opacity
+// gamma = beta * iota * alpha (Eq. 3), multiplied in the order of frag_weights.
+template <class Fn>
+__device__ __forceinline__ void entry_taps_w(const Frame &F, const TileGeom &g, const float4 &pay, Fn &&fn)
+{
+    const int L = g.L;
+    float iota, diota;
+    if (!layer_weight(pay.z, L, F.n_layers, F.eps, iota, diota)) return;
+    const AxisTaps ax = axis_taps(pay.x, L, F.lw[L]);
+    const AxisTaps ay = axis_taps(pay.y, L, F.lh[L]);
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+        if (!(b ? ay.t1 : ay.t0)) continue;
+        const int k = ay.j0 + b - g.y0;
+        if (k < 0 || k >= F.tile_h) continue;
+        const float wy = b ? ay.a : __fsub_rn(1.0f, ay.a);
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            if (!(a ? ax.t1 : ax.t0)) continue;
+            const int j = ax.j0 + a - g.x0;
+            if (j < 0 || j >= F.tile_w) continue;
+            const float wx = a ? ax.a : __fsub_rn(1.0f, ax.a);
+            fn(k * F.tile_w + j, wx * wy * iota * pay.w);
+        }
+    }
+}
+
 // A pixel's kept list: the K smallest keys seen so far in ascending order,
-// with the workspace entry of each; empty slots hold kEmptyKey.
+// each with a 32-bit payload (the forward build keeps the fragment opacity
+// gamma as float bits, the backward the workspace entry); empty slots hold
+// kEmptyKey.
 template <int K>
 struct TopK {
     static_assert(K % 4 == 0, "K must be a multiple of 4");
@@ -175,6 +220,10 @@ struct TopK {
     }
 };
 
+// Small tile lists (at most one entry per thread) are merged without the
+// chunk machinery; each pixel remembers up to kSmallCap covering entries.
+constexpr int kSmallCap = 32;
+
 // Builds the kept list of the thread's pixel (thread t owns pixel t of the
 // tile, t < tile_px); returns the kept count, *nfrag gets the candidates.
 template <int K>
@@ -192,62 +241,27 @@ __device__ int build_topk(const Frame &F, const Workspace &W, int tile, const Ti
     if (beg > end) beg = end;
     unsigned nfr = 0;
     __syncthreads();
-    if (end - beg <= (unsigned)NT && end - beg <= 2u * (unsigned)F.chunk) {
-        // Small list: stage one entry per thread (key, entry, tap footprint),
-        // then every pixel thread scans the staged entries (broadcast reads)
-        // and inserts the ones that cover it.  One barrier, no atomics.
-        const unsigned E = end - beg;
-        unsigned long long *sk = S.ck;
-        unsigned *se = S.ce;
-        unsigned *sm = S.ce + 2 * F.chunk;
-        if ((unsigned)tid < E) {
-            const unsigned e = beg + tid;
-            const float4 pay = W.bucket_pay[e];
-            unsigned foot = 0u;
-            float iota, diota;
-            if (layer_weight(pay.z, g.L, F.n_layers, F.eps, iota, diota)) {
-                const AxisTaps ax = axis_taps(pay.x, g.L, F.lw[g.L]);
-                const AxisTaps ay = axis_taps(pay.y, g.L, F.lh[g.L]);
-                const int dx0 = ax.j0 - g.x0, dy0 = ay.j0 - g.y0;
-                if (dx0 >= -1 && dx0 < F.tile_w && dy0 >= -1 && dy0 < F.tile_h) {
-                    const unsigned xm = (ax.t0 ? 1u : 0u) | (ax.t1 ? 2u : 0u);
-                    const unsigned ym = (ay.t0 ? 1u : 0u) | (ay.t1 ? 2u : 0u);
-                    foot = (unsigned)(dx0 + 1) | ((unsigned)(dy0 + 1) << 7) | (xm << 14) | (ym << 16);
-                }
-            }
-            sk[tid] = W.bucket_key[e];
-            se[tid] = e;
-            sm[tid] = foot;
+    for (unsigned c0 = beg; c0 < end; c0 += (unsigned)F.chunk) {
+        const unsigned n = min(end - c0, (unsigned)F.chunk);
+        // stage the chunk's entries once (coalesced); both passes read them here
+#pragma unroll 4
+        for (unsigned q = tid; q < n; q += NT) {
+            S.sk[q] = W.bucket_key[c0 + q];
+            S.sp[q] = W.bucket_pay[c0 + q];
         }
         __syncthreads();
-        if (owner) {
-            const int tx = tid % F.tile_w, ty = tid / F.tile_w;
-            for (unsigned q = 0; q < E; ++q) {
-                const unsigned v = sm[q];
-                const int dx = tx - ((int)(v & 127u) - 1), dy = ty - ((int)((v >> 7) & 127u) - 1);
-                if ((unsigned)dx < 2u && (unsigned)dy < 2u && ((v >> (14 + dx)) & 1u) && ((v >> (16 + dy)) & 1u)) {
-                    top.insert(sk[q], se[q]);
-                    ++nfr;
-                }
-            }
-        }
-        *nfrag = nfr;
-        return nfr < (unsigned)K ? (int)nfr : K;
-    }
-    for (unsigned c0 = beg; c0 < end; c0 += (unsigned)F.chunk) {
-        const unsigned c1 = min(end, c0 + (unsigned)F.chunk);
-        for (unsigned e = c0 + tid; e < c1; e += NT)
-            entry_taps(F, g, W.bucket_pay[e], [&](int px) { atomicAdd(S.cnt + px, 1u); });
+        for (unsigned q = tid; q < n; q += NT)
+            entry_taps(F, g, S.sp[q], [&](int px) { atomicAdd(S.cnt + px, 1u); });
         __syncthreads();
         const unsigned my = S.cnt[tid];
         S.off[tid] = block_exclusive_scan(my, S.wsum);
         __syncthreads();
-        for (unsigned e = c0 + tid; e < c1; e += NT) {
-            const unsigned long long key = W.bucket_key[e];
-            entry_taps(F, g, W.bucket_pay[e], [&](int px) {
-                const unsigned q = S.off[px] + atomicAdd(S.cur + px, 1u);
-                S.ck[q] = key;
-                S.ce[q] = e;
+        for (unsigned q = tid; q < n; q += NT) {
+            const unsigned long long key = S.sk[q];
+            entry_taps_w(F, g, S.sp[q], [&](int px, float gam) {
+                const unsigned r = S.off[px] + atomicAdd(S.cur + px, 1u);
+                S.ck[r] = key;
+                S.ce[r] = __float_as_uint(gam);
             });
         }
         __syncthreads();
@@ -325,31 +339,26 @@ __global__ void k_tile_blend(Frame F, Workspace W, const DescT *__restrict__ des
         // the largest kept key: the backward's rebuild keeps exactly the keys <= it
         unsigned long long kmax = 0ull;
 #pragma unroll
-        for (int m = 0; m < K; ++m) kmax = top.key[m] != kEmptyKey && top.key[m] > kmax ? top.key[m] : kmax;
+        for (int m = 0; m < K; ++m) {
+            if (m >= nk_warp) break;
+            kmax = m < nk ? top.key[m] : kmax;
+        }
         W.kmax[pix] = kmax;
     }
-    // front to back: weights T_m gamma_m (Eq. 6-7).  Loads go out four
-    // slots at a time, ahead of the dependent arithmetic; unused slots hold
-    // entry 0 and descriptor row 0, valid addresses whose values are ignored.
+    // front to back: weights T_m gamma_m (Eq. 6-7); gamma came with the key.
+    // Descriptor loads go out four slots at a time; unused slots read
+    // descriptor row 0, a valid address whose value is ignored.
     constexpr int B = 4;
     float wgt[K];
     float T = 1.0f;
 #pragma unroll
-    for (int m0 = 0; m0 < K; m0 += B) {
-        if (m0 >= nk_warp) break;
-        float4 pay[B];
-#pragma unroll
-        for (int u = 0; u < B; ++u) pay[u] = W.bucket_pay[top.e[m0 + u]];
-#pragma unroll
-        for (int u = 0; u < B; ++u) {
-            const int m = m0 + u;
-            wgt[m] = 0.0f;
-            if (m < nk) {
-                const FragW w = frag_weights(F, pay[u].x, pay[u].y, pay[u].z, L, j, k);
-                const float gam = w.wx * w.wy * w.iota * pay[u].w;
-                wgt[m] = T * gam;
-                T = T * (1.0f - gam);
-            }
+    for (int m = 0; m < K; ++m) {
+        wgt[m] = 0.0f;
+        if (m >= nk_warp) break;
+        if (m < nk) {
+            const float gam = __uint_as_float(top.e[m]);
+            wgt[m] = T * gam;
+            T = T * (1.0f - gam);
         }
     }
     const int D = F.D;
