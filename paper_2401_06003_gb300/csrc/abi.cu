@@ -82,19 +82,18 @@ tp_status make_frame(const tp_config *cfg, const tp_camera *cam, Frame &F)
     F.tile_base[F.n_layers] = tiles;
     F.n_tiles = tiles;
     // Tile CTAs: one thread per pixel, kept lists in registers; shared memory
-    // holds one chunk of tile-list entries (24 bytes each, staged) and their
-    // fragments (12 bytes each, at most four per entry): 72 bytes per chunk
-    // entry, sized to about 40 KB per CTA.
+    // holds one chunk of tile-list entries' fragments (12 bytes each, at most
+    // four per entry: 48 bytes per chunk entry), sized to about 40 KB per CTA.
     F.tile_px = tw * th;
     F.tile_threads = (F.tile_px + 31) / 32 * 32;
     const int64_t avail = 40 * 1024 - (3 * F.tile_threads + 32) * 4;
-    int64_t chunk = avail / 72;
+    int64_t chunk = avail / 48;
     if (chunk < 128) chunk = 128;
     if (chunk > 2048) chunk = 2048;
     // the backward keeps each pixel's list (16 bytes a slot) in the same region
-    const int64_t need = ((int64_t)16 * F.K * F.tile_px + 71) / 72;
+    const int64_t need = ((int64_t)16 * F.K * F.tile_px + 47) / 48;
     if (chunk < need) chunk = need;
-    chunk = (chunk + 15) / 16 * 16;  // keeps every shared-memory piece 16-byte aligned
+    chunk = (chunk + 15) / 16 * 16;
     F.chunk = (int)chunk;
     if (tpk::tile_smem_bytes(F, true) > kMaxTileSmem) return TP_ERR_UNSUPPORTED;
     return TP_OK;

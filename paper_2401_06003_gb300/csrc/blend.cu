@@ -38,39 +38,30 @@ __device__ __forceinline__ TileGeom tile_geom(const Frame &F, int tile)
     return g;
 }
 
-// Shared-memory layout of a tile CTA (16-byte aligned pieces): the current
-// chunk's fragments grouped by pixel, the chunk's tile-list entries staged
-// from global memory, and the per-pixel counters.  The fragment and staging
-// areas are contiguous (the backward reuses them as one region).
+// Shared-memory layout of a tile CTA: the current chunk's fragments grouped
+// by pixel (keys, then 32-bit payloads) and the per-pixel counters.  Every
+// piece starts on a 16-byte boundary whatever the chunk size.
 struct TileSmem {
     unsigned long long *ck;      // [4 chunk] chunk fragment keys, grouped by pixel
     unsigned *ce;                // [4 chunk] chunk fragment payloads
-    unsigned long long *sk;      // [chunk]   staged entry keys
-    float4 *sp;                  // [chunk]   staged entry payloads
     unsigned *cnt, *off, *cur;   // [tile_threads]
     unsigned *wsum;              // [32]
 };
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
-// Byte offsets of the pieces of the contiguous fragment + staging region;
-// every piece starts on a 16-byte boundary whatever the chunk size.
-__host__ __device__ inline size_t off_ce(size_t C) { return align16(32 * C); }
-__host__ __device__ inline size_t off_sk(size_t C) { return align16(off_ce(C) + 16 * C); }
-__host__ __device__ inline size_t off_sp(size_t C) { return align16(off_sk(C) + 8 * C); }
+// Bytes of the fragment region (the backward reuses it for its kept lists).
 __host__ __device__ inline size_t tile_region_bytes(const Frame &F)
 {
-    return align16(off_sp(F.chunk) + 16 * (size_t)F.chunk);
+    return align16((size_t)32 * F.chunk) + align16((size_t)16 * F.chunk);
 }
 
 __device__ __forceinline__ TileSmem carve(const Frame &F, unsigned char *base)
 {
     TileSmem m;
-    const size_t NT = F.tile_threads, C = F.chunk;
+    const size_t NT = F.tile_threads;
     m.ck = reinterpret_cast<unsigned long long *>(base);
-    m.ce = reinterpret_cast<unsigned *>(base + off_ce(C));
-    m.sk = reinterpret_cast<unsigned long long *>(base + off_sk(C));
-    m.sp = reinterpret_cast<float4 *>(base + off_sp(C));
+    m.ce = reinterpret_cast<unsigned *>(base + align16((size_t)32 * F.chunk));
     m.cnt = reinterpret_cast<unsigned *>(base + tile_region_bytes(F));
     m.off = m.cnt + NT;
     m.cur = m.off + NT;
@@ -242,26 +233,20 @@ __device__ int build_topk(const Frame &F, const Workspace &W, int tile, const Ti
     unsigned nfr = 0;
     __syncthreads();
     for (unsigned c0 = beg; c0 < end; c0 += (unsigned)F.chunk) {
-        const unsigned n = min(end - c0, (unsigned)F.chunk);
-        // stage the chunk's entries once (coalesced); both passes read them here
-#pragma unroll 4
-        for (unsigned q = tid; q < n; q += NT) {
-            S.sk[q] = W.bucket_key[c0 + q];
-            S.sp[q] = W.bucket_pay[c0 + q];
-        }
-        __syncthreads();
-        for (unsigned q = tid; q < n; q += NT)
-            entry_taps(F, g, S.sp[q], [&](int px) { atomicAdd(S.cnt + px, 1u); });
+        const unsigned c1 = min(end, c0 + (unsigned)F.chunk);
+        for (unsigned e = c0 + tid; e < c1; e += NT)
+            entry_taps(F, g, W.bucket_pay[e], [&](int px) { atomicAdd(S.cnt + px, 1u); });
         __syncthreads();
         const unsigned my = S.cnt[tid];
         S.off[tid] = block_exclusive_scan(my, S.wsum);
         __syncthreads();
-        for (unsigned q = tid; q < n; q += NT) {
-            const unsigned long long key = S.sk[q];
-            entry_taps_w(F, g, S.sp[q], [&](int px, float gam) {
-                const unsigned r = S.off[px] + atomicAdd(S.cur + px, 1u);
-                S.ck[r] = key;
-                S.ce[r] = __float_as_uint(gam);
+        for (unsigned e = c0 + tid; e < c1; e += NT) {
+            const unsigned long long key = W.bucket_key[e];
+            const float4 pay = W.bucket_pay[e];
+            entry_taps_w(F, g, pay, [&](int px, float gam) {
+                const unsigned q = S.off[px] + atomicAdd(S.cur + px, 1u);
+                S.ck[q] = key;
+                S.ce[q] = __float_as_uint(gam);
             });
         }
         __syncthreads();
