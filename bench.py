@@ -45,6 +45,8 @@ def parse_args():
     ap.add_argument("--mode", choices=["recompute", "store"], default="recompute")
     ap.add_argument("--tile", default="16x8")
     ap.add_argument("--points", type=int, default=0, help="override the workload's point count (profiling)")
+    ap.add_argument("--desc-dtype", choices=["auto", "f32", "bf16"], default="auto",
+                    help="descriptor storage type (auto: bf16 for the *_bf16 workloads)")
     ap.add_argument("--ref-sample", type=int, default=2_000_000, help="points per reference-arm step")
     ap.add_argument("--cpu-frames", type=int, default=2, help="full oracle frames timed for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -224,7 +226,10 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     sc = scenes.make_config(args.workload, n=args.points or None)
     tw, th = (int(v) for v in args.tile.split("x"))
-    desc_dtype = torch.bfloat16 if args.workload.endswith("bf16") else torch.float32
+    if args.desc_dtype == "auto":
+        desc_dtype = torch.bfloat16 if args.workload.endswith("bf16") else torch.float32
+    else:
+        desc_dtype = torch.bfloat16 if args.desc_dtype == "bf16" else torch.float32
     r = Renderer(sc.camera, sc.n_layers, K=sc.K, D=sc.D, desc_dtype=desc_dtype, mode=args.mode, tile=(tw, th),
                  device=dev)
     N, D, P = sc.n, sc.D, r.P
@@ -377,6 +382,7 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": args.workload, "points": N, "width": sc.camera.width,
                        "height": sc.camera.height, "layers": sc.n_layers, "K": sc.K, "D": D,
+                       "desc_dtype": "bf16" if b == 2 else "f32",
                        "mode": args.mode, "tile": args.tile, "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (216 MB of point inputs per step); no flush"},
             "forward_ms": round(fwd_ms, 4), "fwd_bwd_ms": round(ms_per_step, 4),

@@ -272,3 +272,56 @@ def test_ground6m_full_size_sampled():
     ref = ofr.backward(G[rows].astype(np.float64))
     compare_grads({k: v[sel_pts] for k, v in got.items()}, {k: v[sel_pts] for k, v in ref.items()},
                   name="ground6m sampled")
+
+
+def _crop_pixels(r, rng, n_crops=8, size=64):
+    """Layer-0 pixels of n seeded size x size crops, plus every coarser-layer
+    pixel that covers them."""
+    W, H = r.cam.width, r.cam.height
+    pix = []
+    for _ in range(n_crops):
+        x0 = int(rng.integers(0, W - size))
+        y0 = int(rng.integers(0, H - size))
+        for L in range(r.n_layers):
+            s = 1 << L
+            lw = -(-W // s)
+            xs = np.arange(x0 // s, (x0 + size - 1) // s + 1)
+            ys = np.arange(y0 // s, (y0 + size - 1) // s + 1)
+            yy, xx = np.meshgrid(ys, xs, indexing="ij")
+            pix.append(r.layer_offsets[L] + (yy * lw + xx).ravel())
+    return np.unique(np.concatenate(pix))
+
+
+def test_ground10m_4k_bf16_crops():
+    """10M points at 3840x2160 over 10 layers, 16 bfloat16 descriptor channels:
+    pyramid and gradients on 8 seeded 64x64 crops against the float64 oracle on
+    the original float32 descriptors (1e-2), and against the oracle on the
+    bfloat16 values (float32 tolerances)."""
+    sc = scenes.make_config("ground10m_4k_bf16")
+    r, fr, ins, out = gpu_frame(sc, mode="recompute", desc_dtype=torch.bfloat16)
+    rng = np.random.default_rng(51)
+    pix = _crop_pixels(r, rng)
+    desc_bf = torch.from_numpy(sc.desc).to(torch.bfloat16).to(torch.float32).numpy()
+    o_bf = _oracle(sc, pixels=pix, desc=desc_bf)
+    rows = o_bf.pixels()
+    ref_bf = o_bf.render()
+    compare_forward(out, ref_bf, r.layer_offsets, rows=rows, name="4k bf16 vs oracle(bf16 values)")
+    o_f32 = _oracle(sc, pixels=pix)
+    ref_f = o_f32.render()
+    assert_close_scaled(out["pyramid"][rows], ref_f["pyramid"], BF16_RTOL, name="4k bf16 vs oracle(f32)")
+    err = np.abs(out["pyramid"][rows].astype(np.float64) - ref_f["pyramid"])
+    print(f"4K bf16 crops: pyramid max abs err {err.max():.3e}, mean {err.mean():.3e} "
+          f"(max |value| {np.abs(ref_f['pyramid']).max():.3f})")
+    # loss on the crop pixels only: gradients of every point
+    G = np.zeros((r.P, sc.D), np.float32)
+    G[rows] = rng.uniform(-1, 1, (rows.size, sc.D))
+    got = _gpu_grads(r, fr, ins, G, False)
+    ref_g = o_bf.backward(G[rows].astype(np.float64))
+    touched = np.flatnonzero(np.abs(ref_g["opacity"]) + np.abs(ref_g["desc"]).sum(1) > 0)
+    assert touched.size > 1000
+    compare_grads({k: v[touched] for k, v in got.items()}, {k: v[touched] for k, v in ref_g.items()},
+                  name="4k bf16 crops")
+    ref_gf = o_f32.backward(G[rows].astype(np.float64))
+    for k in ("pos", "size_w", "opacity", "desc"):
+        assert_close_scaled(got[k][touched].reshape(touched.size, -1), ref_gf[k][touched].reshape(touched.size, -1),
+                            BF16_RTOL, name=f"4k bf16 grad_{k} vs oracle(f32)")
