@@ -172,12 +172,12 @@ tp_status from_cuda(cudaError_t e)
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
-// Descriptors can be read four channels at a time when D is a multiple of 4
-// and the rows stay aligned to four elements.
+// Descriptors can be read 16 bytes at a time (4 float32 or 8 bfloat16
+// channels) when D is a multiple of that group and the rows are 16-byte aligned.
 int desc_vector_ok(const tp_config *cfg, const void *desc)
 {
-    const uintptr_t elem = cfg->desc_dtype == TP_BF16 ? 2 : 4;
-    return (cfg->desc_dim % 4) == 0 && ((uintptr_t)desc % (4 * elem)) == 0;
+    const int group = cfg->desc_dtype == TP_BF16 ? 8 : 4;
+    return (cfg->desc_dim % group) == 0 && ((uintptr_t)desc % 16) == 0;
 }
 
 }  // namespace

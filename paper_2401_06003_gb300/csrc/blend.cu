@@ -280,26 +280,43 @@ __device__ __forceinline__ FragW frag_weights(const Frame &F, float x, float y, 
     return w;
 }
 
-// Four channels [d0, d0 + 4) of descriptor i (zeros past D).
+// A group of descriptor channels [d0, d0 + G) of point i, read with one
+// 16-byte load when the rows allow it (G = 4 float32 or 8 bfloat16 channels);
+// channels past D read as zero.
 template <typename DescT>
-__device__ __forceinline__ float4 load_desc4(const DescT *__restrict__ desc, unsigned i, int D, int d0, int vec)
+struct DescGroup {
+    static constexpr int G = sizeof(DescT) == 2 ? 8 : 4;
+    float v[G];
+};
+
+template <typename DescT>
+__device__ __forceinline__ DescGroup<DescT> load_group(const DescT *__restrict__ desc, unsigned i, int D, int d0,
+                                                       int vec)
 {
+    DescGroup<DescT> r;
     const DescT *p = desc + (long long)i * D + d0;
     if (vec) {
         if constexpr (sizeof(DescT) == 4) {
-            return __ldg(reinterpret_cast<const float4 *>(p));
+            const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+            r.v[0] = a.x;
+            r.v[1] = a.y;
+            r.v[2] = a.z;
+            r.v[3] = a.w;
         } else {
-            const uint2 raw = __ldg(reinterpret_cast<const uint2 *>(p));
-            const __nv_bfloat162 lo = *reinterpret_cast<const __nv_bfloat162 *>(&raw.x);
-            const __nv_bfloat162 hi = *reinterpret_cast<const __nv_bfloat162 *>(&raw.y);
-            const float2 a = __bfloat1622float2(lo), b = __bfloat1622float2(hi);
-            return make_float4(a.x, a.y, b.x, b.y);
-        }
-    }
-    float v[4];
+            const uint4 raw = __ldg(reinterpret_cast<const uint4 *>(p));
+            const unsigned w[4] = {raw.x, raw.y, raw.z, raw.w};
 #pragma unroll
-    for (int c = 0; c < 4; ++c) v[c] = d0 + c < D ? load_desc(p + c) : 0.0f;
-    return make_float4(v[0], v[1], v[2], v[3]);
+            for (int c = 0; c < 4; ++c) {
+                const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w[c]));
+                r.v[2 * c] = f.x;
+                r.v[2 * c + 1] = f.y;
+            }
+        }
+        return r;
+    }
+#pragma unroll
+    for (int c = 0; c < DescGroup<DescT>::G; ++c) r.v[c] = d0 + c < D ? load_desc(p + c) : 0.0f;
+    return r;
 }
 
 template <int K, typename DescT>
@@ -347,33 +364,35 @@ __global__ void k_tile_blend(Frame F, Workspace W, const DescT *__restrict__ des
         }
     }
     const int D = F.D;
-    for (int d0 = 0; d0 < D; d0 += 4) {
-        float4 c = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    constexpr int G = DescGroup<DescT>::G;
+    for (int d0 = 0; d0 < D; d0 += G) {
+        float c[G];
+#pragma unroll
+        for (int q = 0; q < G; ++q) c[q] = 0.0f;
 #pragma unroll
         for (int m0 = 0; m0 < K; m0 += B) {
             if (m0 >= nk_warp) break;
-            float4 t[B];
+            DescGroup<DescT> t[B];
 #pragma unroll
             for (int u = 0; u < B; ++u)
-                t[u] = load_desc4(desc, m0 + u < nk ? (unsigned)(top.key[m0 + u] & 0xFFFFFFFFull) : 0u, D, d0,
+                t[u] = load_group(desc, m0 + u < nk ? (unsigned)(top.key[m0 + u] & 0xFFFFFFFFull) : 0u, D, d0,
                                   F.desc_vec);
 #pragma unroll
             for (int u = 0; u < B; ++u) {
                 if (m0 + u < nk) {
-                    c.x += wgt[m0 + u] * t[u].x;
-                    c.y += wgt[m0 + u] * t[u].y;
-                    c.z += wgt[m0 + u] * t[u].z;
-                    c.w += wgt[m0 + u] * t[u].w;
+#pragma unroll
+                    for (int q = 0; q < G; ++q) c[q] += wgt[m0 + u] * t[u].v[q];
                 }
             }
         }
         if (active) {
             float *out = pyramid + pix * D + d0;
             if (F.desc_vec) {
-                *reinterpret_cast<float4 *>(out) = c;
+#pragma unroll
+                for (int q = 0; q < G; q += 4)
+                    *reinterpret_cast<float4 *>(out + q) = make_float4(c[q], c[q + 1], c[q + 2], c[q + 3]);
             } else {
-                const float cv[4] = {c.x, c.y, c.z, c.w};
-                for (int q = 0; q < 4 && d0 + q < D; ++q) out[q] = cv[q];
+                for (int q = 0; q < G && d0 + q < D; ++q) out[q] = c[q];
             }
         }
     }
@@ -398,25 +417,25 @@ __device__ __forceinline__ void atomic_add4(float *p, float4 v)
 
 // Adjoint of one kept fragment, given its forward quantities; scatters the
 // point gradients.  G is the pixel's dL/dC; R the running back-to-front term.
-// t0 holds channels [0, 4) of the point's descriptor, loaded by the caller.
+// t0 holds the first channel group of the point's descriptor, loaded by the caller.
 template <typename DescT>
 __device__ __forceinline__ void adjoint_fragment(const Frame &F, int L, int j, int k, unsigned i, float x, float y,
                                                  float z, float s, float al, float Tm, const float *G, float &R,
-                                                 float4 t0, const DescT *__restrict__ desc, float *__restrict__ gpos,
-                                                 float *__restrict__ gsw, float *__restrict__ gop,
-                                                 float *__restrict__ gdesc)
+                                                 const DescGroup<DescT> &t0, const DescT *__restrict__ desc,
+                                                 float *__restrict__ gpos, float *__restrict__ gsw,
+                                                 float *__restrict__ gop, float *__restrict__ gdesc)
 {
     const int D = F.D;
+    constexpr int NG = DescGroup<DescT>::G;
     const FragW w = frag_weights(F, x, y, s, L, j, k);
     const float beta = w.wx * w.wy;
     const float gam = beta * w.iota * al;
     float gdot = 0.0f;
-    for (int d0 = 0; d0 < D; d0 += 4) {
-        const float4 t = d0 == 0 ? t0 : load_desc4(desc, i, D, d0, F.desc_vec);
-        gdot += G[d0] * t.x;
-        if (d0 + 1 < D) gdot += G[d0 + 1] * t.y;
-        if (d0 + 2 < D) gdot += G[d0 + 2] * t.z;
-        if (d0 + 3 < D) gdot += G[d0 + 3] * t.w;
+    for (int d0 = 0; d0 < D; d0 += NG) {
+        const DescGroup<DescT> t = d0 == 0 ? t0 : load_group(desc, i, D, d0, F.desc_vec);
+#pragma unroll
+        for (int q = 0; q < NG; ++q)
+            if (d0 + q < D) gdot += G[d0 + q] * t.v[q];
     }
     const float dg = Tm * (gdot - R);
     R = gam * gdot + (1.0f - gam) * R;
@@ -514,13 +533,14 @@ __global__ void k_tile_backward(Frame F, Workspace W, const DescT *__restrict__ 
     constexpr int B = 4;
     for (int m1 = nk - 1; m1 >= 0; m1 -= B) {
         unsigned long long key[B];
-        float4 pay[B], t0[B];
+        float4 pay[B];
+        DescGroup<DescT> t0[B];
 #pragma unroll
         for (int u = 0; u < B; ++u) {
             const int m = m1 - u >= 0 ? m1 - u : 0;
             key[u] = kk[m * TP + tid];
             pay[u] = W.bucket_pay[ke[m * TP + tid]];
-            t0[u] = load_desc4(desc, (unsigned)(key[u] & 0xFFFFFFFFull), D, 0, F.desc_vec);
+            t0[u] = load_group(desc, (unsigned)(key[u] & 0xFFFFFFFFull), D, 0, F.desc_vec);
         }
 #pragma unroll
         for (int u = 0; u < B; ++u) {
@@ -576,7 +596,7 @@ __global__ void __launch_bounds__(kBlock) k_stored_backward(Frame F, long long P
             const unsigned i = kept[pix * K + m];
             const float4 r = rec[i];
             adjoint_fragment<DescT>(F, L, j, k, i, r.x, r.y, r.z, r.w, __ldg(opacity + i), Tm[m], G, R,
-                                    load_desc4(desc, i, F.D, 0, F.desc_vec), desc, gpos, gsw, gop, gdesc);
+                                    load_group(desc, i, F.D, 0, F.desc_vec), desc, gpos, gsw, gop, gdesc);
         }
     }
 }
