@@ -395,6 +395,131 @@ def run_ours(args):
 
 
 # ---------------------------------------------------------------------------
+# batched multi-view (16 orbit cameras of uneven resolution, one graph)
+# ---------------------------------------------------------------------------
+
+def run_batch(args):
+    import torch
+
+    from paper_2401_06003_gb300 import BatchRenderer, Renderer, autotune_tiles, scenes
+    from paper_2401_06003_gb300.build import build as build_lib
+
+    build_lib()
+    rank, world, local = dist_setup(True)
+    dev = torch.device("cuda", local)
+    sc = scenes.make_config(args.workload, n=args.points or None)
+    N, D, V = sc.n, sc.D, len(sc.cameras)
+    pos = torch.from_numpy(sc.pos).to(dev)
+    sw = torch.from_numpy(sc.size_w).to(dev)
+    op = torch.from_numpy(sc.opacity).to(dev)
+    desc = torch.from_numpy(sc.desc).to(dev)
+    t0 = time.perf_counter()
+    tiles, tuning = autotune_tiles(sc.cameras, sc.n_layers, pos, sw, op, desc, K=sc.K, device=dev)
+    tune_s = time.perf_counter() - t0
+    br = BatchRenderer(sc.cameras, sc.n_layers, K=sc.K, D=D, tiles=tiles, device=dev)
+    ws = br.new_workspace(N)
+    rec = torch.empty((V, N, 4), device=dev)
+    pyr = torch.empty((br.P, D), device=dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(4321 + rank)
+    G = (torch.rand((br.P, D), generator=gen, device=dev) * 2 - 1).contiguous()
+    grads = (torch.empty((N, 3), device=dev), torch.empty((N,), device=dev), torch.empty((N,), device=dev),
+             torch.empty((N, D), device=dev))
+
+    def step():
+        br.project(pos, sw, ws, records=rec)
+        br.splat_forward(rec, op, ws)
+        br.blend(N, desc, ws, pyramid=pyr)
+        br.splat_backward(rec, op, desc, G, ws, grads=grads)
+
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.current_stream(dev).wait_stream(side)
+    torch.cuda.synchronize(dev)
+    if br.status(ws):
+        raise RuntimeError("device status flags set after warm-up")
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    for _ in range(2):
+        graph.replay()
+    stream = torch.cuda.current_stream(dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(torch.cuda.current_device()) if not args.no_clocks else None
+    barrier(world, dev)
+    torch.cuda.synchronize(dev)
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for s_ in range(args.steps):
+        evs[s_][0].record(stream)
+        graph.replay()
+        evs[s_][1].record(stream)
+    a1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world, dev)
+    clk = clocks.stop() if clocks else None
+    total_ms = max_over_ranks(a0.elapsed_time(a1), world, dev)
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+    ms_per_step = total_ms / args.steps
+    value = V * N * world / (ms_per_step * 1e-3) / 1e6
+
+    # per-view latency: each view rendered alone (forward + backward), same tiles
+    per_view = []
+    for v, cam in enumerate(sc.cameras):
+        r = Renderer(cam, sc.n_layers, K=sc.K, D=D, tile=tiles[v], device=dev)
+        wsv = r.new_workspace(N)
+        recv = torch.empty((N, 4), device=dev)
+        pyrv = torch.empty((r.P, D), device=dev)
+        Gv = br.view(G, v).contiguous()
+        times = []
+        for it in range(args.warmup + args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r.project(pos, sw, wsv, records=recv)
+            r.splat_forward(recv, op, wsv)
+            r.blend(N, desc, wsv, pyramid=pyrv)
+            r.splat_backward(recv, op, desc, Gv, wsv, grads=grads)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            if it >= args.warmup:
+                times.append(e0.elapsed_time(e1))
+        per_view.append({"view": v, "width": cam.width, "height": cam.height, "tile": list(tiles[v]),
+                         "p50_ms": round(float(np.percentile(times, 50)), 4),
+                         "p99_ms": round(float(np.percentile(times, 99)), 4)})
+        del wsv, recv, pyrv
+    if rank == 0:
+        line = {
+            "metric": "batched multi-view fwd+bwd: aggregate Mpoints/s (views x points), 16 orbit views",
+            "value": round(value, 3), "unit": "Mpoints/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "points": N, "views": V,
+                       "resolutions": [[c.width, c.height] for c in sc.cameras], "layers": sc.n_layers,
+                       "K": sc.K, "D": D, "mode": "recompute", "graph": "one CUDA graph per fwd+bwd batch step",
+                       "l2": "inputs larger than L2; no flush"},
+            "batch_step_ms": {"p50": round(float(np.percentile(step_ms, 50)), 4),
+                              "p99": round(float(np.percentile(step_ms, 99)), 4)},
+            "per_view": per_view,
+            "per_view_p50_ms": round(float(np.percentile([p["p50_ms"] for p in per_view], 50)), 4),
+            "per_view_p99_ms": round(float(np.percentile([p["p99_ms"] for p in per_view], 99)), 4),
+            "sum_of_single_view_p50_ms": round(sum(p["p50_ms"] for p in per_view), 4),
+            "autotune": {"seconds": round(tune_s, 2),
+                         "ms_by_resolution": {f"{w}x{h}": {f"{a}x{b}": round(t, 4) for (a, b), t in d.items()}
+                                              for (w, h), d in tuning.items()}},
+            "gpu_launches": 6 * args.steps, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
 # the CPU oracle (cpu_baseline leg and the reference arm)
 # ---------------------------------------------------------------------------
 
@@ -460,6 +585,8 @@ def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload.endswith("orbit16"):
+        run_batch(args)
     else:
         run_ours(args)
 

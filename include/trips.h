@@ -215,6 +215,49 @@ TP_API tp_status tp_splat_backward(const tp_config *cfg, const tp_camera *cam, i
                             const float *grad_pyramid, float *grad_pos, float *grad_size_w, float *grad_opacity,
                             float *grad_desc, void *ws, int64_t ws_bytes, tp_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Batches of views.  Up to TP_MAX_VIEWS cameras (each with its own
+ * resolution and screen tile) are rendered from one point cloud by the same
+ * launches: each of the four stages is one kernel launch over all views, so
+ * a whole frame batch can be captured as one CUDA graph.  The calls mirror
+ * the single-view ones with these differences:
+ *   cams [n_views] (host): one camera per view; all views share cfg.
+ *   tiles [n_views][2] (host, nullable): tile_w, tile_h of each view (0 = the
+ *     default); NULL uses cfg->tile_w / cfg->tile_h for every view.
+ *   records [n_views][n][4]: the projection of every point in every view.
+ *   pyramid, grad_pyramid [P_total][D], kept [P_total][K] ...: the views'
+ *     pyramids concatenated in view order; view v starts at row
+ *     view_offsets[v] of tp_batch_pixels.
+ *   grad_* [n][...]: the gradient of the sum of the views' losses.
+ * The workspace is sized by tp_batch_workspace_bytes (default capacity
+ * 8 n n_views tile-list entries, which cannot overflow).
+ * ------------------------------------------------------------------------ */
+#define TP_MAX_VIEWS 16
+
+TP_API int64_t tp_batch_pixels(const tp_camera *cams, int32_t n_views, int32_t n_layers, int64_t *view_offsets);
+
+TP_API int64_t tp_batch_workspace_bytes(const tp_config *cfg, const tp_camera *cams, const int32_t *tiles,
+                                        int32_t n_views, int64_t n_points, int64_t entry_capacity);
+
+TP_API tp_status tp_batch_project(const tp_config *cfg, const tp_camera *cams, const int32_t *tiles, int32_t n_views,
+                                  int64_t n, const float *pos, const float *size_w, float *records, void *ws,
+                                  int64_t ws_bytes, tp_stream_t stream);
+
+TP_API tp_status tp_batch_splat_forward(const tp_config *cfg, const tp_camera *cams, const int32_t *tiles,
+                                        int32_t n_views, int64_t n, const float *records, const float *opacity,
+                                        void *ws, int64_t ws_bytes, tp_stream_t stream);
+
+TP_API tp_status tp_batch_blend(const tp_config *cfg, const tp_camera *cams, const int32_t *tiles, int32_t n_views,
+                                int64_t n, const void *desc, float *pyramid, uint32_t *kept, uint8_t *n_kept,
+                                float *t_final, uint32_t *n_frag, void *ws, int64_t ws_bytes, tp_stream_t stream);
+
+TP_API tp_status tp_batch_splat_backward(const tp_config *cfg, const tp_camera *cams, const int32_t *tiles,
+                                         int32_t n_views, int64_t n, const float *records, const float *opacity,
+                                         const void *desc, const uint32_t *kept, const uint8_t *n_kept,
+                                         const float *grad_pyramid, float *grad_pos, float *grad_size_w,
+                                         float *grad_opacity, float *grad_desc, void *ws, int64_t ws_bytes,
+                                         tp_stream_t stream);
+
 /*
  * Synchronises `stream` and reads the workspace's device status word into
  * *device_flags (host; TP_FLAG_* bits).  Returns TP_ERR_CAPACITY,

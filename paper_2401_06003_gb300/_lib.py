@@ -56,6 +56,16 @@ _SIGS = {
                                 _P, _I64, _P]),
     "tp_splat_backward": (ctypes.c_int, [ctypes.POINTER(tp_config), ctypes.POINTER(tp_camera), _I64, _P, _P, _P, _P,
                                          _P, _P, _P, _P, _P, _P, _P, _I64, _P]),
+    "tp_batch_pixels": (_I64, [_P, ctypes.c_int32, ctypes.c_int32, _P]),
+    "tp_batch_workspace_bytes": (_I64, [ctypes.POINTER(tp_config), _P, _P, ctypes.c_int32, _I64, _I64]),
+    "tp_batch_project": (ctypes.c_int, [ctypes.POINTER(tp_config), _P, _P, ctypes.c_int32, _I64, _P, _P, _P, _P,
+                                        _I64, _P]),
+    "tp_batch_splat_forward": (ctypes.c_int, [ctypes.POINTER(tp_config), _P, _P, ctypes.c_int32, _I64, _P, _P, _P,
+                                              _I64, _P]),
+    "tp_batch_blend": (ctypes.c_int, [ctypes.POINTER(tp_config), _P, _P, ctypes.c_int32, _I64, _P, _P, _P, _P, _P,
+                                      _P, _P, _I64, _P]),
+    "tp_batch_splat_backward": (ctypes.c_int, [ctypes.POINTER(tp_config), _P, _P, ctypes.c_int32, _I64, _P, _P, _P,
+                                               _P, _P, _P, _P, _P, _P, _P, _P, _I64, _P]),
     "tp_get_status": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int32)]),
     "tp_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "tp_version": (ctypes.c_int32, []),

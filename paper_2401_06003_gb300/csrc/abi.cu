@@ -1,8 +1,9 @@
 // abi.cu -- the extern "C" entry points declared in include/trips.h.
 //
-// Host-side argument checks, the frame description (pyramid layout and
-// screen-tile table), the workspace layout, and the kernel launches.  No
-// call allocates, frees or synchronises, except tp_get_status.
+// Host-side argument checks, the frame description of every view (pyramid
+// layout and screen-tile table), the workspace layout, and the kernel
+// launches.  A single view is a batch of one.  No call allocates, frees or
+// synchronises, except tp_get_status.
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -11,7 +12,9 @@
 
 namespace {
 
+using tpk::Batch;
 using tpk::Frame;
+using tpk::kMaxViews;
 using tpk::Workspace;
 
 constexpr int64_t kAlign = 256;
@@ -43,10 +46,9 @@ void fill_layers(const tp_camera *cam, int n_layers, Frame &F)
     }
 }
 
-// Builds the frame description; TP_OK or the reason it is invalid.
-tp_status make_frame(const tp_config *cfg, const tp_camera *cam, Frame &F)
+tp_status check_config(const tp_config *cfg)
 {
-    if (!cfg || !valid_camera(cam)) return TP_ERR_INVALID_ARG;
+    if (!cfg) return TP_ERR_INVALID_ARG;
     if (cfg->n_layers < 1 || cfg->n_layers > tpk::kMaxLayers) return TP_ERR_INVALID_ARG;
     if (cfg->desc_dim < 1 || cfg->desc_dim > 64) return TP_ERR_INVALID_ARG;
     if (!(cfg->eps >= 0.0f && cfg->eps <= 1.0f)) return TP_ERR_INVALID_ARG;
@@ -54,9 +56,20 @@ tp_status make_frame(const tp_config *cfg, const tp_camera *cam, Frame &F)
     if (cfg->mode != TP_STORE_LISTS && cfg->mode != TP_RECOMPUTE) return TP_ERR_INVALID_ARG;
     if (cfg->K < 1 || cfg->K > 255) return TP_ERR_INVALID_ARG;
     if (cfg->K != 4 && cfg->K != 8 && cfg->K != 16 && cfg->K != 32) return TP_ERR_UNSUPPORTED;
-    const int tw = cfg->tile_w > 0 ? cfg->tile_w : 16;
-    const int th = cfg->tile_h > 0 ? cfg->tile_h : 8;
-    if (tw > 64 || th > 64 || cfg->tile_w < 0 || cfg->tile_h < 0) return TP_ERR_INVALID_ARG;
+    if (cfg->tile_w < 0 || cfg->tile_h < 0) return TP_ERR_INVALID_ARG;
+    return TP_OK;
+}
+
+// The frame description of one view with screen tiles of tw x th pixels
+// (0 = the default 16 x 8).
+tp_status make_frame(const tp_config *cfg, const tp_camera *cam, int tw, int th, Frame &F)
+{
+    tp_status st = check_config(cfg);
+    if (st != TP_OK) return st;
+    if (!valid_camera(cam)) return TP_ERR_INVALID_ARG;
+    if (tw == 0) tw = 16;
+    if (th == 0) th = 8;
+    if (tw < 0 || th < 0 || tw > 64 || th > 64) return TP_ERR_INVALID_ARG;
     if (tw * th > 1024) return TP_ERR_UNSUPPORTED;  // one thread per tile pixel
     std::memset(&F, 0, sizeof(F));
     F.fx = cam->fx; F.fy = cam->fy; F.cx = cam->cx; F.cy = cam->cy;
@@ -76,7 +89,7 @@ tp_status make_frame(const tp_config *cfg, const tp_camera *cam, Frame &F)
         F.tiles_x[L] = (F.lw[L] + tw - 1) / tw;
         F.tiles_y[L] = (F.lh[L] + th - 1) / th;
         const int64_t t = (int64_t)tiles + (int64_t)F.tiles_x[L] * F.tiles_y[L];
-        if (t > (1 << 30)) return TP_ERR_INVALID_ARG;
+        if (t > (1 << 28)) return TP_ERR_INVALID_ARG;
         tiles = (int)t;
     }
     F.tile_base[F.n_layers] = tiles;
@@ -93,55 +106,83 @@ tp_status make_frame(const tp_config *cfg, const tp_camera *cam, Frame &F)
     // the backward keeps each pixel's list (16 bytes a slot) in the same region
     const int64_t need = ((int64_t)16 * F.K * F.tile_px + 47) / 48;
     if (chunk < need) chunk = need;
-    chunk = (chunk + 15) / 16 * 16;
-    F.chunk = (int)chunk;
+    F.chunk = (int)((chunk + 15) / 16 * 16);
     if (tpk::tile_smem_bytes(F, true) > kMaxTileSmem) return TP_ERR_UNSUPPORTED;
     return TP_OK;
 }
 
-// Workspace: status word, tile counts, tile offsets, fill cursors, the
-// per-pixel largest kept keys, then the tile lists as two arrays: 8-byte
-// fragment keys and 16-byte payloads.
+// The batch description of n_views views; tiles is [n_views][2] tile shapes
+// or NULL (the config's tile shape for every view).
+template <int MaxV>
+tp_status make_batch(const tp_config *cfg, const tp_camera *cams, const int32_t *tiles, int n_views, Batch<MaxV> &B)
+{
+    if (!cfg || !cams || n_views < 1 || n_views > MaxV) return TP_ERR_INVALID_ARG;
+    std::memset(&B, 0, sizeof(B));
+    B.n_views = n_views;
+    for (int v = 0; v < n_views; ++v) {
+        const int tw = tiles ? tiles[2 * v] : cfg->tile_w;
+        const int th = tiles ? tiles[2 * v + 1] : cfg->tile_h;
+        tp_status st = make_frame(cfg, cams + v, tw, th, B.view[v]);
+        if (st != TP_OK) return st;
+        const Frame &F = B.view[v];
+        B.tile_base[v + 1] = B.tile_base[v] + F.n_tiles;
+        B.pix_base[v + 1] = B.pix_base[v] + F.pix_base[F.n_layers];
+        if (F.tile_threads > B.max_threads) B.max_threads = F.tile_threads;
+        if ((int64_t)B.tile_base[v + 1] > ((int64_t)1 << 28)) return TP_ERR_INVALID_ARG;
+    }
+    B.n_tiles = B.tile_base[n_views];
+    B.n_pix = B.pix_base[n_views];
+    // the launch's block is the largest tile CTA; every view's region must fit with it
+    for (int v = 0; v < n_views; ++v) {
+        Frame G = B.view[v];
+        G.tile_threads = B.max_threads;
+        if (tpk::tile_smem_bytes(G, true) > kMaxTileSmem) return TP_ERR_UNSUPPORTED;
+    }
+    return TP_OK;
+}
+
+// Workspace: status word, tile counts [T][copies], tile offsets [T + 1],
+// fill cursors [T][copies], the per-pixel largest kept keys [P], then the tile
+// lists as two arrays: 8-byte fragment keys and 16-byte payloads.
 constexpr int64_t kEntryBytes = 24;
 
 struct WsLayout {
     int64_t count, off, cursor, kmax, key, pay, end;
 };
 
-WsLayout layout_for(const Frame &F, int64_t capacity)
+WsLayout layout_for(int64_t n_tiles, int64_t n_pix, int64_t capacity)
 {
     WsLayout w;
-    const int64_t T = F.n_tiles;
     w.count = kAlign;
-    w.off = align_up(w.count + 4 * T * tpk::kCopies);
-    w.cursor = align_up(w.off + 4 * (T + 1));
-    w.kmax = align_up(w.cursor + 4 * T * tpk::kCopies);
-    w.key = align_up(w.kmax + 8 * (int64_t)F.pix_base[F.n_layers]);
+    w.off = align_up(w.count + 4 * n_tiles * tpk::kCopies);
+    w.cursor = align_up(w.off + 4 * (n_tiles + 1));
+    w.kmax = align_up(w.cursor + 4 * n_tiles * tpk::kCopies);
+    w.key = align_up(w.kmax + 8 * n_pix);
     w.pay = align_up(w.key + 8 * capacity);
     w.end = w.pay + 16 * capacity;
     return w;
 }
 
 // Entry capacity that fits in ws_bytes (largest c with layout_for(c).end <= ws_bytes).
-int64_t capacity_for(const Frame &F, int64_t ws_bytes)
+int64_t capacity_for(int64_t n_tiles, int64_t n_pix, int64_t ws_bytes)
 {
-    const WsLayout w0 = layout_for(F, 0);
+    const WsLayout w0 = layout_for(n_tiles, n_pix, 0);
     if (ws_bytes < w0.end) return -1;
     // align_up only adds bytes, so (ws_bytes - key) / 24 is an upper bound;
     // alignment costs < 256 bytes, so the loop runs at most ~11 times.
     int64_t c = (ws_bytes - w0.key) / kEntryBytes;
     if (c < 0) c = 0;
-    while (c > 0 && layout_for(F, c).end > ws_bytes) --c;
+    while (c > 0 && layout_for(n_tiles, n_pix, c).end > ws_bytes) --c;
     if (c > 0x7FFFFFFF) c = 0x7FFFFFFF;
     return c;
 }
 
-tp_status bind_workspace(const Frame &F, void *ws, int64_t ws_bytes, Workspace &W)
+tp_status bind_workspace(int64_t n_tiles, int64_t n_pix, void *ws, int64_t ws_bytes, Workspace &W)
 {
     if (!ws || ((uintptr_t)ws % kAlign) != 0) return TP_ERR_INVALID_ARG;
-    const int64_t cap = capacity_for(F, ws_bytes);
+    const int64_t cap = capacity_for(n_tiles, n_pix, ws_bytes);
     if (cap < 1) return TP_ERR_INVALID_ARG;
-    const WsLayout w = layout_for(F, cap);
+    const WsLayout w = layout_for(n_tiles, n_pix, cap);
     char *base = static_cast<char *>(ws);
     W.status = reinterpret_cast<unsigned *>(base);
     W.tile_count = reinterpret_cast<unsigned *>(base + w.count);
@@ -154,13 +195,14 @@ tp_status bind_workspace(const Frame &F, void *ws, int64_t ws_bytes, Workspace &
     return TP_OK;
 }
 
-tp_status common_checks(const tp_config *cfg, const tp_camera *cam, int64_t n, void *ws, int64_t ws_bytes,
-                        Frame &F, Workspace &W)
+template <int MaxV>
+tp_status batch_checks(const tp_config *cfg, const tp_camera *cams, const int32_t *tiles, int n_views, int64_t n,
+                       void *ws, int64_t ws_bytes, Batch<MaxV> &B, Workspace &W)
 {
     if (n < 0 || n >= kMaxPoints) return TP_ERR_INVALID_ARG;
-    tp_status s = make_frame(cfg, cam, F);
+    tp_status s = make_batch(cfg, cams, tiles, n_views, B);
     if (s != TP_OK) return s;
-    return bind_workspace(F, ws, ws_bytes, W);
+    return bind_workspace(B.n_tiles, B.n_pix, ws, ws_bytes, W);
 }
 
 tp_status from_cuda(cudaError_t e)
@@ -180,6 +222,97 @@ int desc_vector_ok(const tp_config *cfg, const void *desc)
     return (cfg->desc_dim % group) == 0 && ((uintptr_t)desc % 16) == 0;
 }
 
+template <int MaxV>
+void set_vec_flags(Batch<MaxV> &B, int desc_vec, int grad_vec)
+{
+    for (int v = 0; v < B.n_views; ++v) {
+        B.view[v].desc_vec = desc_vec;
+        B.view[v].grad_vec = grad_vec;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The four stages over a batch of views.
+// ---------------------------------------------------------------------------
+
+template <int MaxV>
+tp_status do_project(const tp_config *cfg, const tp_camera *cams, const int32_t *tiles, int n_views, int64_t n,
+                     const float *pos, const float *size_w, float *records, void *ws, int64_t ws_bytes,
+                     tp_stream_t stream)
+{
+    Batch<MaxV> B;
+    Workspace W;
+    tp_status s = batch_checks(cfg, cams, tiles, n_views, n, ws, ws_bytes, B, W);
+    if (s != TP_OK) return s;
+    if (n > 0 && (!pos || !size_w || !records || !aligned16(records))) return TP_ERR_INVALID_ARG;
+    return from_cuda(tpk::launch_project_count(B, W, n, pos, size_w, reinterpret_cast<float4 *>(records),
+                                               (cudaStream_t)stream));
+}
+
+template <int MaxV>
+tp_status do_splat_forward(const tp_config *cfg, const tp_camera *cams, const int32_t *tiles, int n_views, int64_t n,
+                           const float *records, const float *opacity, void *ws, int64_t ws_bytes,
+                           tp_stream_t stream)
+{
+    Batch<MaxV> B;
+    Workspace W;
+    tp_status s = batch_checks(cfg, cams, tiles, n_views, n, ws, ws_bytes, B, W);
+    if (s != TP_OK) return s;
+    if (n > 0 && (!records || !opacity || !aligned16(records))) return TP_ERR_INVALID_ARG;
+    return from_cuda(tpk::launch_scan_fill(B, W, n, reinterpret_cast<const float4 *>(records), opacity,
+                                           (cudaStream_t)stream));
+}
+
+template <int MaxV>
+tp_status do_blend(const tp_config *cfg, const tp_camera *cams, const int32_t *tiles, int n_views, int64_t n,
+                   const void *desc, float *pyramid, uint32_t *kept, uint8_t *n_kept, float *t_final,
+                   uint32_t *n_frag, void *ws, int64_t ws_bytes, tp_stream_t stream)
+{
+    Batch<MaxV> B;
+    Workspace W;
+    tp_status s = batch_checks(cfg, cams, tiles, n_views, n, ws, ws_bytes, B, W);
+    if (s != TP_OK) return s;
+    if (!pyramid) return TP_ERR_INVALID_ARG;
+    if (n > 0 && !desc) return TP_ERR_INVALID_ARG;
+    set_vec_flags(B, desc_vector_ok(cfg, desc) && aligned16(pyramid), 0);
+    return from_cuda(tpk::launch_blend(B, W, desc, cfg->desc_dtype, pyramid, kept, n_kept, t_final, n_frag,
+                                       (cudaStream_t)stream));
+}
+
+template <int MaxV>
+tp_status do_backward(const tp_config *cfg, const tp_camera *cams, const int32_t *tiles, int n_views, int64_t n,
+                      const float *records, const float *opacity, const void *desc, const uint32_t *kept,
+                      const uint8_t *n_kept, const float *grad_pyramid, float *grad_pos, float *grad_size_w,
+                      float *grad_opacity, float *grad_desc, void *ws, int64_t ws_bytes, tp_stream_t stream)
+{
+    Batch<MaxV> B;
+    Workspace W;
+    tp_status s = batch_checks(cfg, cams, tiles, n_views, n, ws, ws_bytes, B, W);
+    if (s != TP_OK) return s;
+    if ((kept == nullptr) != (n_kept == nullptr)) return TP_ERR_INVALID_ARG;
+    if (!grad_pyramid) return TP_ERR_INVALID_ARG;
+    if (n > 0 && (!records || !opacity || !desc || !grad_pos || !grad_size_w || !grad_opacity || !grad_desc ||
+                  !aligned16(records)))
+        return TP_ERR_INVALID_ARG;
+    set_vec_flags(B, desc_vector_ok(cfg, desc), (cfg->desc_dim % 4) == 0 && aligned16(grad_desc));
+    return from_cuda(tpk::launch_backward(B, W, n, reinterpret_cast<const float4 *>(records), opacity, desc,
+                                          cfg->desc_dtype, kept, n_kept, grad_pyramid, grad_pos, grad_size_w,
+                                          grad_opacity, grad_desc, (cudaStream_t)stream));
+}
+
+template <int MaxV>
+int64_t batch_workspace_bytes(const tp_config *cfg, const tp_camera *cams, const int32_t *tiles, int n_views,
+                              int64_t n_points, int64_t entry_capacity)
+{
+    Batch<MaxV> B;
+    if (n_points < 0 || n_points >= kMaxPoints) return -1;
+    if (make_batch(cfg, cams, tiles, n_views, B) != TP_OK) return -1;
+    int64_t cap = entry_capacity > 0 ? entry_capacity : 8 * n_points * n_views;
+    if (cap < 1) cap = 1;
+    if (cap > 0x7FFFFFFF) cap = 0x7FFFFFFF;
+    return layout_for(B.n_tiles, B.n_pix, cap).end;
+}
+
 }  // namespace
 
 extern "C" {
@@ -197,52 +330,26 @@ int64_t tp_pyramid_pixels(const tp_camera *cam, int32_t n_layers, int64_t *layer
 
 int64_t tp_workspace_bytes(const tp_config *cfg, const tp_camera *cam, int64_t n_points, int64_t entry_capacity)
 {
-    Frame F;
-    if (n_points < 0 || n_points >= kMaxPoints) return -1;
-    if (make_frame(cfg, cam, F) != TP_OK) return -1;
-    int64_t cap = entry_capacity > 0 ? entry_capacity : 8 * n_points;
-    if (cap < 1) cap = 1;
-    if (cap > 0x7FFFFFFF) cap = 0x7FFFFFFF;
-    return layout_for(F, cap).end;
+    return batch_workspace_bytes<1>(cfg, cam, nullptr, 1, n_points, entry_capacity);
 }
 
 tp_status tp_project(const tp_config *cfg, const tp_camera *cam, int64_t n, const float *pos, const float *size_w,
                      float *records, void *ws, int64_t ws_bytes, tp_stream_t stream)
 {
-    Frame F;
-    Workspace W;
-    tp_status s = common_checks(cfg, cam, n, ws, ws_bytes, F, W);
-    if (s != TP_OK) return s;
-    if (n > 0 && (!pos || !size_w || !records || !aligned16(records))) return TP_ERR_INVALID_ARG;
-    return from_cuda(tpk::launch_project_count(F, W, n, pos, size_w, reinterpret_cast<float4 *>(records),
-                                               (cudaStream_t)stream));
+    return do_project<1>(cfg, cam, nullptr, 1, n, pos, size_w, records, ws, ws_bytes, stream);
 }
 
 tp_status tp_splat_forward(const tp_config *cfg, const tp_camera *cam, int64_t n, const float *records,
                            const float *opacity, void *ws, int64_t ws_bytes, tp_stream_t stream)
 {
-    Frame F;
-    Workspace W;
-    tp_status s = common_checks(cfg, cam, n, ws, ws_bytes, F, W);
-    if (s != TP_OK) return s;
-    if (n > 0 && (!records || !opacity || !aligned16(records))) return TP_ERR_INVALID_ARG;
-    return from_cuda(tpk::launch_scan_fill(F, W, n, reinterpret_cast<const float4 *>(records), opacity,
-                                           (cudaStream_t)stream));
+    return do_splat_forward<1>(cfg, cam, nullptr, 1, n, records, opacity, ws, ws_bytes, stream);
 }
 
 tp_status tp_blend(const tp_config *cfg, const tp_camera *cam, int64_t n, const void *desc, float *pyramid,
                    uint32_t *kept, uint8_t *n_kept, float *t_final, uint32_t *n_frag, void *ws, int64_t ws_bytes,
                    tp_stream_t stream)
 {
-    Frame F;
-    Workspace W;
-    tp_status s = common_checks(cfg, cam, n, ws, ws_bytes, F, W);
-    if (s != TP_OK) return s;
-    if (!pyramid) return TP_ERR_INVALID_ARG;
-    if (n > 0 && !desc) return TP_ERR_INVALID_ARG;
-    F.desc_vec = desc_vector_ok(cfg, desc) && aligned16(pyramid);
-    return from_cuda(tpk::launch_blend(F, W, desc, cfg->desc_dtype, pyramid, kept, n_kept, t_final, n_frag,
-                                       (cudaStream_t)stream));
+    return do_blend<1>(cfg, cam, nullptr, 1, n, desc, pyramid, kept, n_kept, t_final, n_frag, ws, ws_bytes, stream);
 }
 
 tp_status tp_splat_backward(const tp_config *cfg, const tp_camera *cam, int64_t n, const float *records,
@@ -250,20 +357,61 @@ tp_status tp_splat_backward(const tp_config *cfg, const tp_camera *cam, int64_t 
                             const float *grad_pyramid, float *grad_pos, float *grad_size_w, float *grad_opacity,
                             float *grad_desc, void *ws, int64_t ws_bytes, tp_stream_t stream)
 {
-    Frame F;
-    Workspace W;
-    tp_status s = common_checks(cfg, cam, n, ws, ws_bytes, F, W);
-    if (s != TP_OK) return s;
-    if ((kept == nullptr) != (n_kept == nullptr)) return TP_ERR_INVALID_ARG;
-    if (!grad_pyramid) return TP_ERR_INVALID_ARG;
-    if (n > 0 && (!records || !opacity || !desc || !grad_pos || !grad_size_w || !grad_opacity || !grad_desc ||
-                  !aligned16(records)))
-        return TP_ERR_INVALID_ARG;
-    F.desc_vec = desc_vector_ok(cfg, desc);
-    F.grad_vec = (cfg->desc_dim % 4) == 0 && aligned16(grad_desc);
-    return from_cuda(tpk::launch_backward(F, W, n, reinterpret_cast<const float4 *>(records), opacity, desc,
-                                          cfg->desc_dtype, kept, n_kept, grad_pyramid, grad_pos, grad_size_w,
-                                          grad_opacity, grad_desc, (cudaStream_t)stream));
+    return do_backward<1>(cfg, cam, nullptr, 1, n, records, opacity, desc, kept, n_kept, grad_pyramid, grad_pos,
+                          grad_size_w, grad_opacity, grad_desc, ws, ws_bytes, stream);
+}
+
+int64_t tp_batch_pixels(const tp_camera *cams, int32_t n_views, int32_t n_layers, int64_t *view_offsets)
+{
+    if (!cams || n_views < 1 || n_views > kMaxViews) return -1;
+    int64_t total = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const int64_t p = tp_pyramid_pixels(cams + v, n_layers, nullptr);
+        if (p < 0) return -1;
+        if (view_offsets) view_offsets[v] = total;
+        total += p;
+    }
+    if (view_offsets) view_offsets[n_views] = total;
+    return total;
+}
+
+int64_t tp_batch_workspace_bytes(const tp_config *cfg, const tp_camera *cams, const int32_t *tiles, int32_t n_views,
+                                 int64_t n_points, int64_t entry_capacity)
+{
+    return batch_workspace_bytes<kMaxViews>(cfg, cams, tiles, n_views, n_points, entry_capacity);
+}
+
+tp_status tp_batch_project(const tp_config *cfg, const tp_camera *cams, const int32_t *tiles, int32_t n_views,
+                           int64_t n, const float *pos, const float *size_w, float *records, void *ws,
+                           int64_t ws_bytes, tp_stream_t stream)
+{
+    return do_project<kMaxViews>(cfg, cams, tiles, n_views, n, pos, size_w, records, ws, ws_bytes, stream);
+}
+
+tp_status tp_batch_splat_forward(const tp_config *cfg, const tp_camera *cams, const int32_t *tiles, int32_t n_views,
+                                 int64_t n, const float *records, const float *opacity, void *ws, int64_t ws_bytes,
+                                 tp_stream_t stream)
+{
+    return do_splat_forward<kMaxViews>(cfg, cams, tiles, n_views, n, records, opacity, ws, ws_bytes, stream);
+}
+
+tp_status tp_batch_blend(const tp_config *cfg, const tp_camera *cams, const int32_t *tiles, int32_t n_views,
+                         int64_t n, const void *desc, float *pyramid, uint32_t *kept, uint8_t *n_kept,
+                         float *t_final, uint32_t *n_frag, void *ws, int64_t ws_bytes, tp_stream_t stream)
+{
+    return do_blend<kMaxViews>(cfg, cams, tiles, n_views, n, desc, pyramid, kept, n_kept, t_final, n_frag, ws,
+                               ws_bytes, stream);
+}
+
+tp_status tp_batch_splat_backward(const tp_config *cfg, const tp_camera *cams, const int32_t *tiles,
+                                  int32_t n_views, int64_t n, const float *records, const float *opacity,
+                                  const void *desc, const uint32_t *kept, const uint8_t *n_kept,
+                                  const float *grad_pyramid, float *grad_pos, float *grad_size_w,
+                                  float *grad_opacity, float *grad_desc, void *ws, int64_t ws_bytes,
+                                  tp_stream_t stream)
+{
+    return do_backward<kMaxViews>(cfg, cams, tiles, n_views, n, records, opacity, desc, kept, n_kept, grad_pyramid,
+                                  grad_pos, grad_size_w, grad_opacity, grad_desc, ws, ws_bytes, stream);
 }
 
 tp_status tp_get_status(const void *ws, tp_stream_t stream, int32_t *device_flags)
@@ -294,6 +442,6 @@ const char *tp_status_string(tp_status status)
     return "unknown status";
 }
 
-int32_t tp_version(void) { return 100; }
+int32_t tp_version(void) { return 110; }
 
 }  // extern "C"

@@ -37,10 +37,17 @@ __device__ __forceinline__ void for_each_tile(const Frame &F, const float4 &r, F
 }
 
 // Collect: project, cull, write the record and count (point, tile) pairs.
-__global__ void __launch_bounds__(kBlock) k_project_count(Frame F, Workspace W, long long n,
-                                                          const float *__restrict__ pos,
-                                                          const float *__restrict__ size_w, float4 *__restrict__ rec)
+// blockIdx.y is the view; view v writes records rec[v n + i] and counts into
+// its own range of global tiles.
+template <int MaxV>
+__global__ void __launch_bounds__(kBlock) k_project_count(const __grid_constant__ Batch<MaxV> B, Workspace W,
+                                                          long long n, const float *__restrict__ pos,
+                                                          const float *__restrict__ size_w, float4 *__restrict__ rec_all)
 {
+    const int v = MaxV > 1 ? (int)blockIdx.y : 0;
+    const Frame &F = B.view[v];
+    float4 *__restrict__ rec = rec_all + (long long)v * n;
+    unsigned *__restrict__ count = W.tile_count + (size_t)B.tile_base[v] * kCopies;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const float X = __ldg(pos + 3 * i), Y = __ldg(pos + 3 * i + 1), Z = __ldg(pos + 3 * i + 2);
@@ -54,17 +61,17 @@ __global__ void __launch_bounds__(kBlock) k_project_count(Frame F, Workspace W, 
         }
         rec[i] = r;
         const unsigned c = (unsigned)(i & (kCopies - 1));
-        for_each_tile(F, r, [&](int t) { atomicAdd(W.tile_count + (size_t)t * kCopies + c, 1u); });
+        for_each_tile(F, r, [&](int t) { atomicAdd(count + (size_t)t * kCopies + c, 1u); });
     }
 }
 
 // One warp per tile: the copies' exclusive prefix becomes each copy's fill
 // cursor, and the tile's total goes to tile_off[t] for the offset scan.
-__global__ void __launch_bounds__(kBlock) k_tile_totals(Frame F, Workspace W)
+__global__ void __launch_bounds__(kBlock) k_tile_totals(int n_tiles, Workspace W)
 {
     const int t = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
-    if (t >= F.n_tiles) return;
+    if (t >= n_tiles) return;
     const unsigned v = W.tile_count[(size_t)t * kCopies + lane];
     unsigned x = v;
 #pragma unroll
@@ -77,10 +84,10 @@ __global__ void __launch_bounds__(kBlock) k_tile_totals(Frame F, Workspace W)
 }
 
 // Offset scan of the tile totals, in place (one CTA; the tile count is small).
-__global__ void __launch_bounds__(1024) k_scan_tiles(Frame F, Workspace W)
+__global__ void __launch_bounds__(1024) k_scan_tiles(int n_tiles, Workspace W)
 {
     __shared__ unsigned warp_tot[32];
-    const int T = F.n_tiles;
+    const int T = n_tiles;
     const int per = (T + blockDim.x - 1) / blockDim.x;
     const int beg = min(T, (int)threadIdx.x * per);
     const int end = min(T, beg + per);
@@ -121,9 +128,15 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Frame F, Workspace W)
 
 // Splat: every point appends its fragment key (z, i) and its blend payload
 // (x, y, s, alpha) to the list of each tile it touches.
-__global__ void __launch_bounds__(kBlock) k_fill(Frame F, Workspace W, long long n, const float4 *__restrict__ rec,
-                                                 const float *__restrict__ opacity)
+template <int MaxV>
+__global__ void __launch_bounds__(kBlock) k_fill(const __grid_constant__ Batch<MaxV> B, Workspace W, long long n,
+                                                 const float4 *__restrict__ rec_all, const float *__restrict__ opacity)
 {
+    const int v = MaxV > 1 ? (int)blockIdx.y : 0;
+    const Frame &F = B.view[v];
+    const float4 *__restrict__ rec = rec_all + (long long)v * n;
+    const unsigned *__restrict__ tile_off = W.tile_off + B.tile_base[v];
+    unsigned *__restrict__ cursor = W.tile_cursor + (size_t)B.tile_base[v] * kCopies;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const float4 r = rec[i];
@@ -132,7 +145,7 @@ __global__ void __launch_bounds__(kBlock) k_fill(Frame F, Workspace W, long long
         const float4 pay = make_float4(r.x, r.y, r.w, __ldg(opacity + i));
         const unsigned c = (unsigned)(i & (kCopies - 1));
         for_each_tile(F, r, [&](int t) {
-            const unsigned e = W.tile_off[t] + atomicAdd(W.tile_cursor + (size_t)t * kCopies + c, 1u);
+            const unsigned e = tile_off[t] + atomicAdd(cursor + (size_t)t * kCopies + c, 1u);
             if (e < W.capacity) {
                 W.bucket_key[e] = key;
                 W.bucket_pay[e] = pay;
@@ -149,30 +162,43 @@ static int grid_for(long long n)
     return (int)b;
 }
 
-cudaError_t launch_project_count(const Frame &F, const Workspace &W, long long n, const float *pos,
+template <int MaxV>
+cudaError_t launch_project_count(const Batch<MaxV> &B, const Workspace &W, long long n, const float *pos,
                                  const float *size_w, float4 *rec, cudaStream_t stream)
 {
     cudaError_t e = cudaMemsetAsync(W.status, 0, sizeof(unsigned), stream);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(W.tile_count, 0, sizeof(unsigned) * kCopies * (size_t)F.n_tiles, stream);
+    e = cudaMemsetAsync(W.tile_count, 0, sizeof(unsigned) * kCopies * (size_t)B.n_tiles, stream);
     if (e != cudaSuccess) return e;
     if (n == 0) return cudaSuccess;
-    k_project_count<<<grid_for(n), kBlock, 0, stream>>>(F, W, n, pos, size_w, rec);
+    const dim3 grid(grid_for(n), B.n_views);
+    k_project_count<MaxV><<<grid, kBlock, 0, stream>>>(B, W, n, pos, size_w, rec);
     return cudaGetLastError();
 }
 
-cudaError_t launch_scan_fill(const Frame &F, const Workspace &W, long long n, const float4 *rec,
+template <int MaxV>
+cudaError_t launch_scan_fill(const Batch<MaxV> &B, const Workspace &W, long long n, const float4 *rec,
                              const float *opacity, cudaStream_t stream)
 {
-    const long long threads = (long long)F.n_tiles * 32;
-    k_tile_totals<<<(int)((threads + kBlock - 1) / kBlock), kBlock, 0, stream>>>(F, W);
+    const long long threads = (long long)B.n_tiles * 32;
+    k_tile_totals<<<(int)((threads + kBlock - 1) / kBlock), kBlock, 0, stream>>>(B.n_tiles, W);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_scan_tiles<<<1, 1024, 0, stream>>>(F, W);
+    k_scan_tiles<<<1, 1024, 0, stream>>>(B.n_tiles, W);
     e = cudaGetLastError();
     if (e != cudaSuccess || n == 0) return e;
-    k_fill<<<grid_for(n), kBlock, 0, stream>>>(F, W, n, rec, opacity);
+    const dim3 grid(grid_for(n), B.n_views);
+    k_fill<MaxV><<<grid, kBlock, 0, stream>>>(B, W, n, rec, opacity);
     return cudaGetLastError();
 }
+
+template cudaError_t launch_project_count<1>(const Batch<1> &, const Workspace &, long long, const float *,
+                                             const float *, float4 *, cudaStream_t);
+template cudaError_t launch_project_count<kMaxViews>(const Batch<kMaxViews> &, const Workspace &, long long,
+                                                     const float *, const float *, float4 *, cudaStream_t);
+template cudaError_t launch_scan_fill<1>(const Batch<1> &, const Workspace &, long long, const float4 *,
+                                         const float *, cudaStream_t);
+template cudaError_t launch_scan_fill<kMaxViews>(const Batch<kMaxViews> &, const Workspace &, long long,
+                                                 const float4 *, const float *, cudaStream_t);
 
 }  // namespace tpk

@@ -56,10 +56,12 @@ __host__ __device__ inline size_t tile_region_bytes(const Frame &F)
     return align16((size_t)32 * F.chunk) + align16((size_t)16 * F.chunk);
 }
 
+// The counters are sized by the launch's block (the largest tile CTA of the
+// batch), which may exceed this view's own tile_threads.
 __device__ __forceinline__ TileSmem carve(const Frame &F, unsigned char *base)
 {
     TileSmem m;
-    const size_t NT = F.tile_threads;
+    const size_t NT = blockDim.x;
     m.ck = reinterpret_cast<unsigned long long *>(base);
     m.ce = reinterpret_cast<unsigned *>(base + align16((size_t)32 * F.chunk));
     m.cnt = reinterpret_cast<unsigned *>(base + tile_region_bytes(F));
@@ -319,15 +321,18 @@ __device__ __forceinline__ DescGroup<DescT> load_group(const DescT *__restrict__
     return r;
 }
 
-template <int K, typename DescT>
-__global__ void k_tile_blend(Frame F, Workspace W, const DescT *__restrict__ desc, float *__restrict__ pyramid,
-                             unsigned *__restrict__ kept, unsigned char *__restrict__ n_kept,
-                             float *__restrict__ t_final, unsigned *__restrict__ n_frag)
+template <int K, typename DescT, int MaxV>
+__global__ void k_tile_blend(const __grid_constant__ Batch<MaxV> B, Workspace W, const DescT *__restrict__ desc,
+                             float *__restrict__ pyramid, unsigned *__restrict__ kept,
+                             unsigned char *__restrict__ n_kept, float *__restrict__ t_final,
+                             unsigned *__restrict__ n_frag)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tile = blockIdx.x;  // global over the batch
+    const int v = view_of_tile(B, tile);
+    const Frame &F = B.view[v];
     const TileSmem S = carve(F, smem_raw);
-    const int tile = blockIdx.x;
-    const TileGeom g = tile_geom(F, tile);
+    const TileGeom g = tile_geom(F, tile - B.tile_base[v]);
     TopK<K> top;
     unsigned nfr;
     int nk = build_topk<K>(F, W, tile, g, S, top, &nfr);
@@ -336,7 +341,7 @@ __global__ void k_tile_blend(Frame F, Workspace W, const DescT *__restrict__ des
     const bool active = tid < TP && j < F.lw[L] && k < F.lh[L];
     if (!active) nk = 0;
     const int nk_warp = __reduce_max_sync(0xffffffffu, nk);
-    const long long pix = F.pix_base[L] + (long long)k * F.lw[L] + j;
+    const long long pix = B.pix_base[v] + F.pix_base[L] + (long long)k * F.lw[L] + j;
     if (active) {
         // the largest kept key: the backward's rebuild keeps exactly the keys <= it
         unsigned long long kmax = 0ull;
@@ -350,7 +355,7 @@ __global__ void k_tile_blend(Frame F, Workspace W, const DescT *__restrict__ des
     // front to back: weights T_m gamma_m (Eq. 6-7); gamma came with the key.
     // Descriptor loads go out four slots at a time; unused slots read
     // descriptor row 0, a valid address whose value is ignored.
-    constexpr int B = 4;
+    constexpr int NB = 4;
     float wgt[K];
     float T = 1.0f;
 #pragma unroll
@@ -370,15 +375,15 @@ __global__ void k_tile_blend(Frame F, Workspace W, const DescT *__restrict__ des
 #pragma unroll
         for (int q = 0; q < G; ++q) c[q] = 0.0f;
 #pragma unroll
-        for (int m0 = 0; m0 < K; m0 += B) {
+        for (int m0 = 0; m0 < K; m0 += NB) {
             if (m0 >= nk_warp) break;
-            DescGroup<DescT> t[B];
+            DescGroup<DescT> t[NB];
 #pragma unroll
-            for (int u = 0; u < B; ++u)
+            for (int u = 0; u < NB; ++u)
                 t[u] = load_group(desc, m0 + u < nk ? (unsigned)(top.key[m0 + u] & 0xFFFFFFFFull) : 0u, D, d0,
                                   F.desc_vec);
 #pragma unroll
-            for (int u = 0; u < B; ++u) {
+            for (int u = 0; u < NB; ++u) {
                 if (m0 + u < nk) {
 #pragma unroll
                     for (int q = 0; q < G; ++q) c[q] += wgt[m0 + u] * t[u].v[q];
@@ -468,19 +473,21 @@ __device__ __forceinline__ void adjoint_fragment(const Frame &F, int L, int j, i
 // fragment into one of its pixel's K slots (no selection work), each pixel's
 // thread sorts its at most K slots, and runs the adjoint of its blend back to
 // front in a rolled loop.
-template <int K, typename DescT>
-__global__ void k_tile_backward(Frame F, Workspace W, const DescT *__restrict__ desc,
+template <int K, typename DescT, int MaxV>
+__global__ void k_tile_backward(const __grid_constant__ Batch<MaxV> B, Workspace W, const DescT *__restrict__ desc,
                                 const float *__restrict__ grad_pyr, float *__restrict__ gpos, float *__restrict__ gsw,
                                 float *__restrict__ gop, float *__restrict__ gdesc)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int tile = blockIdx.x;  // global over the batch
+    const int v = view_of_tile(B, tile);
+    const Frame &F = B.view[v];
     const TileSmem S = carve(F, smem_raw);
-    const int tile = blockIdx.x;
-    const TileGeom g = tile_geom(F, tile);
+    const TileGeom g = tile_geom(F, tile - B.tile_base[v]);
     const int TP = F.tile_px, tid = threadIdx.x, NT = blockDim.x, L = g.L, D = F.D;
     const int j = g.x0 + tid % F.tile_w, k = g.y0 + tid / F.tile_w;
     const bool active = tid < TP && j < F.lw[L] && k < F.lh[L];
-    const long long pix = F.pix_base[L] + (long long)k * F.lw[L] + j;
+    const long long pix = B.pix_base[v] + F.pix_base[L] + (long long)k * F.lw[L] + j;
     // slot-major private slots in the chunk area: key [K][TP], entry [K][TP], T_m [K][TP]
     unsigned long long *kk = S.ck;
     unsigned *ke = reinterpret_cast<unsigned *>(S.ck + (size_t)K * TP);
@@ -530,20 +537,20 @@ __global__ void k_tile_backward(Frame F, Workspace W, const DescT *__restrict__ 
     for (int d = 0; d < D; ++d) G[d] = __ldg(grad_pyr + pix * D + d);
     // back to front, four slots at a time: the loads of a batch go out first
     float R = 0.0f;
-    constexpr int B = 4;
-    for (int m1 = nk - 1; m1 >= 0; m1 -= B) {
-        unsigned long long key[B];
-        float4 pay[B];
-        DescGroup<DescT> t0[B];
+    constexpr int NB = 4;
+    for (int m1 = nk - 1; m1 >= 0; m1 -= NB) {
+        unsigned long long key[NB];
+        float4 pay[NB];
+        DescGroup<DescT> t0[NB];
 #pragma unroll
-        for (int u = 0; u < B; ++u) {
+        for (int u = 0; u < NB; ++u) {
             const int m = m1 - u >= 0 ? m1 - u : 0;
             key[u] = kk[m * TP + tid];
             pay[u] = W.bucket_pay[ke[m * TP + tid]];
             t0[u] = load_group(desc, (unsigned)(key[u] & 0xFFFFFFFFull), D, 0, F.desc_vec);
         }
 #pragma unroll
-        for (int u = 0; u < B; ++u) {
+        for (int u = 0; u < NB; ++u) {
             const int m = m1 - u;
             if (m < 0) break;
             adjoint_fragment<DescT>(F, L, j, k, (unsigned)(key[u] & 0xFFFFFFFFull), pay[u].x, pay[u].y,
@@ -554,8 +561,9 @@ __global__ void k_tile_backward(Frame F, Workspace W, const DescT *__restrict__ 
 }
 
 // Backward with the lists stored by the blend kernel.
-template <int K, typename DescT>
-__global__ void __launch_bounds__(kBlock) k_stored_backward(Frame F, long long P, const float4 *__restrict__ rec,
+template <int K, typename DescT, int MaxV>
+__global__ void __launch_bounds__(kBlock) k_stored_backward(const __grid_constant__ Batch<MaxV> B, long long n,
+                                                            const float4 *__restrict__ rec_all,
                                                             const float *__restrict__ opacity,
                                                             const DescT *__restrict__ desc,
                                                             const unsigned *__restrict__ kept,
@@ -565,13 +573,17 @@ __global__ void __launch_bounds__(kBlock) k_stored_backward(Frame F, long long P
                                                             float *__restrict__ gop, float *__restrict__ gdesc)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x; pix < P; pix += stride) {
+    for (long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x; pix < B.n_pix; pix += stride) {
         int nk = n_kept[pix];
         if (nk == 0) continue;
         if (nk > K) nk = K;
+        const int v = view_of_pixel(B, pix);
+        const Frame &F = B.view[v];
+        const float4 *__restrict__ rec = rec_all + (long long)v * n;
+        const long long vpix = pix - B.pix_base[v];
         int L = 0;
-        while (L + 1 < F.n_layers && pix >= F.pix_base[L + 1]) ++L;
-        const long long local = pix - F.pix_base[L];
+        while (L + 1 < F.n_layers && vpix >= F.pix_base[L + 1]) ++L;
+        const long long local = vpix - F.pix_base[L];
         const int j = (int)(local % F.lw[L]), k = (int)(local / F.lw[L]);
         float Tm[K];
         float T = 1.0f;
@@ -618,39 +630,49 @@ static cudaError_t prepare_tile_kernel(KernelT kernel, size_t smem_bytes, int th
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
 }
 
-template <int K, typename DescT>
-static cudaError_t blend_impl(const Frame &F, const Workspace &W, const void *desc, float *pyramid, unsigned *kept,
-                              unsigned char *n_kept, float *t_final, unsigned *n_frag, cudaStream_t stream)
+// Shared memory of a tile launch: the largest fragment region over the views
+// plus counters for the launch's block.
+template <int MaxV>
+static size_t batch_smem(const Batch<MaxV> &B)
 {
-    const size_t smem = tile_smem_bytes(F, false);
-    cudaError_t e = prepare_tile_kernel(k_tile_blend<K, DescT>, smem, F.tile_threads);
+    size_t region = 0;
+    for (int v = 0; v < B.n_views; ++v) region = region > tile_region_bytes(B.view[v]) ? region : tile_region_bytes(B.view[v]);
+    return region + (3 * (size_t)B.max_threads + 32) * sizeof(unsigned);
+}
+
+template <int K, typename DescT, int MaxV>
+static cudaError_t blend_impl(const Batch<MaxV> &B, const Workspace &W, const void *desc, float *pyramid,
+                              unsigned *kept, unsigned char *n_kept, float *t_final, unsigned *n_frag,
+                              cudaStream_t stream)
+{
+    const size_t smem = batch_smem(B);
+    cudaError_t e = prepare_tile_kernel(k_tile_blend<K, DescT, MaxV>, smem, B.max_threads);
     if (e != cudaSuccess) return e;
-    k_tile_blend<K, DescT><<<F.n_tiles, F.tile_threads, smem, stream>>>(
-        F, W, static_cast<const DescT *>(desc), pyramid, kept, n_kept, t_final, n_frag);
+    k_tile_blend<K, DescT, MaxV><<<B.n_tiles, B.max_threads, smem, stream>>>(
+        B, W, static_cast<const DescT *>(desc), pyramid, kept, n_kept, t_final, n_frag);
     return cudaGetLastError();
 }
 
-template <int K, typename DescT>
-static cudaError_t backward_impl(const Frame &F, const Workspace &W, const float4 *rec, const float *opacity,
-                                 const void *desc, const unsigned *kept, const unsigned char *n_kept,
-                                 const float *grad_pyr, float *gpos, float *gsw, float *gop, float *gdesc,
-                                 cudaStream_t stream)
+template <int K, typename DescT, int MaxV>
+static cudaError_t backward_impl(const Batch<MaxV> &B, const Workspace &W, long long n, const float4 *rec,
+                                 const float *opacity, const void *desc, const unsigned *kept,
+                                 const unsigned char *n_kept, const float *grad_pyr, float *gpos, float *gsw,
+                                 float *gop, float *gdesc, cudaStream_t stream)
 {
     const DescT *d = static_cast<const DescT *>(desc);
     if (kept) {
-        const long long P = F.pix_base[F.n_layers];
-        long long blocks = (P + kBlock - 1) / kBlock;
+        long long blocks = (B.n_pix + kBlock - 1) / kBlock;
         if (blocks > 152 * 32) blocks = 152 * 32;
         if (blocks < 1) blocks = 1;
-        k_stored_backward<K, DescT><<<(int)blocks, kBlock, 0, stream>>>(F, P, rec, opacity, d, kept, n_kept,
-                                                                        grad_pyr, gpos, gsw, gop, gdesc);
+        k_stored_backward<K, DescT, MaxV><<<(int)blocks, kBlock, 0, stream>>>(B, n, rec, opacity, d, kept, n_kept,
+                                                                              grad_pyr, gpos, gsw, gop, gdesc);
         return cudaGetLastError();
     }
-    const size_t smem = tile_smem_bytes(F, true);
-    cudaError_t e = prepare_tile_kernel(k_tile_backward<K, DescT>, smem, F.tile_threads);
+    const size_t smem = batch_smem(B);
+    cudaError_t e = prepare_tile_kernel(k_tile_backward<K, DescT, MaxV>, smem, B.max_threads);
     if (e != cudaSuccess) return e;
-    k_tile_backward<K, DescT><<<F.n_tiles, F.tile_threads, smem, stream>>>(F, W, d, grad_pyr, gpos, gsw, gop,
-                                                                           gdesc);
+    k_tile_backward<K, DescT, MaxV><<<B.n_tiles, B.max_threads, smem, stream>>>(B, W, d, grad_pyr, gpos, gsw,
+                                                                                 gop, gdesc);
     return cudaGetLastError();
 }
 
@@ -663,41 +685,59 @@ static cudaError_t backward_impl(const Frame &F, const Workspace &W, const float
     default: return cudaErrorInvalidValue;                          \
     }
 
-cudaError_t launch_blend(const Frame &F, const Workspace &W, const void *desc, int desc_dtype, float *pyramid,
-                         unsigned *kept, unsigned char *n_kept, float *t_final, unsigned *n_frag,
+template <int MaxV>
+cudaError_t launch_blend(const Batch<MaxV> &B, const Workspace &W, const void *desc, int desc_dtype,
+                         float *pyramid, unsigned *kept, unsigned char *n_kept, float *t_final, unsigned *n_frag,
                          cudaStream_t stream)
 {
+    const int K = B.view[0].K;
     if (desc_dtype == TP_BF16) {
-        TPK_DISPATCH_K(F.K, return (blend_impl<KC, __nv_bfloat16>(F, W, desc, pyramid, kept, n_kept, t_final,
-                                                                 n_frag, stream)));
+        TPK_DISPATCH_K(K, return (blend_impl<KC, __nv_bfloat16, MaxV>(B, W, desc, pyramid, kept, n_kept, t_final,
+                                                                     n_frag, stream)));
     } else {
-        TPK_DISPATCH_K(F.K, return (blend_impl<KC, float>(F, W, desc, pyramid, kept, n_kept, t_final, n_frag,
-                                                         stream)));
+        TPK_DISPATCH_K(K, return (blend_impl<KC, float, MaxV>(B, W, desc, pyramid, kept, n_kept, t_final, n_frag,
+                                                             stream)));
     }
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_backward(const Frame &F, const Workspace &W, long long n, const float4 *rec,
+template <int MaxV>
+cudaError_t launch_backward(const Batch<MaxV> &B, const Workspace &W, long long n, const float4 *rec,
                             const float *opacity, const void *desc, int desc_dtype, const unsigned *kept,
                             const unsigned char *n_kept, const float *grad_pyramid, float *grad_pos,
                             float *grad_sw, float *grad_opacity, float *grad_desc, cudaStream_t stream)
 {
     cudaError_t e;
     if (n == 0) return cudaSuccess;
+    const int K = B.view[0].K, D = B.view[0].D;
     if ((e = cudaMemsetAsync(grad_pos, 0, sizeof(float) * 3 * (size_t)n, stream)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(grad_sw, 0, sizeof(float) * (size_t)n, stream)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(grad_opacity, 0, sizeof(float) * (size_t)n, stream)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(grad_desc, 0, sizeof(float) * (size_t)F.D * (size_t)n, stream)) != cudaSuccess)
+    if ((e = cudaMemsetAsync(grad_desc, 0, sizeof(float) * (size_t)D * (size_t)n, stream)) != cudaSuccess)
         return e;
     if (desc_dtype == TP_BF16) {
-        TPK_DISPATCH_K(F.K, return (backward_impl<KC, __nv_bfloat16>(F, W, rec, opacity, desc, kept, n_kept,
-                                                                    grad_pyramid, grad_pos, grad_sw, grad_opacity,
-                                                                    grad_desc, stream)));
+        TPK_DISPATCH_K(K, return (backward_impl<KC, __nv_bfloat16, MaxV>(B, W, n, rec, opacity, desc, kept, n_kept,
+                                                                        grad_pyramid, grad_pos, grad_sw,
+                                                                        grad_opacity, grad_desc, stream)));
     } else {
-        TPK_DISPATCH_K(F.K, return (backward_impl<KC, float>(F, W, rec, opacity, desc, kept, n_kept, grad_pyramid,
-                                                            grad_pos, grad_sw, grad_opacity, grad_desc, stream)));
+        TPK_DISPATCH_K(K, return (backward_impl<KC, float, MaxV>(B, W, n, rec, opacity, desc, kept, n_kept,
+                                                                grad_pyramid, grad_pos, grad_sw, grad_opacity,
+                                                                grad_desc, stream)));
     }
     return cudaErrorInvalidValue;
 }
+
+template cudaError_t launch_blend<1>(const Batch<1> &, const Workspace &, const void *, int, float *, unsigned *,
+                                     unsigned char *, float *, unsigned *, cudaStream_t);
+template cudaError_t launch_blend<kMaxViews>(const Batch<kMaxViews> &, const Workspace &, const void *, int,
+                                             float *, unsigned *, unsigned char *, float *, unsigned *,
+                                             cudaStream_t);
+template cudaError_t launch_backward<1>(const Batch<1> &, const Workspace &, long long, const float4 *,
+                                        const float *, const void *, int, const unsigned *, const unsigned char *,
+                                        const float *, float *, float *, float *, float *, cudaStream_t);
+template cudaError_t launch_backward<kMaxViews>(const Batch<kMaxViews> &, const Workspace &, long long,
+                                                const float4 *, const float *, const void *, int,
+                                                const unsigned *, const unsigned char *, const float *, float *,
+                                                float *, float *, float *, cudaStream_t);
 
 }  // namespace tpk

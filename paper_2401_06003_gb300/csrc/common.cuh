@@ -42,6 +42,42 @@ struct Frame {
     long long pix_base[kMaxLayers + 1];            // first pyramid pixel of each layer
 };
 
+// A batch of views rendered by the same launches: view v owns global tiles
+// [tile_base[v], tile_base[v+1]) and global pyramid pixels
+// [pix_base[v], pix_base[v+1]); its point records are rows [v n, (v+1) n).
+// Passed to the kernels by value (MaxV = 1 for a single view, kMaxViews for
+// batches; 16 views take about 10 KB of kernel parameters).
+constexpr int kMaxViews = 16;
+
+template <int MaxV>
+struct Batch {
+    int n_views;
+    int n_tiles;          // tiles over all views
+    long long n_pix;      // pyramid pixels over all views
+    int max_threads;      // largest tile CTA over the views
+    int tile_base[MaxV + 1];
+    long long pix_base[MaxV + 1];
+    Frame view[MaxV];
+};
+
+template <int MaxV>
+__device__ __forceinline__ int view_of_tile(const Batch<MaxV> &B, int tile)
+{
+    int v = 0;
+    if constexpr (MaxV > 1)
+        while (v + 1 < B.n_views && tile >= B.tile_base[v + 1]) ++v;
+    return v;
+}
+
+template <int MaxV>
+__device__ __forceinline__ int view_of_pixel(const Batch<MaxV> &B, long long pix)
+{
+    int v = 0;
+    if constexpr (MaxV > 1)
+        while (v + 1 < B.n_views && pix >= B.pix_base[v + 1]) ++v;
+    return v;
+}
+
 // Device pointers into the caller's workspace.
 // Every tile counter exists in kCopies copies; point i uses copy i % kCopies.
 // Hot tiles (thousands of points near the horizon) would otherwise serialise
@@ -237,19 +273,23 @@ __device__ __forceinline__ float load_desc<__nv_bfloat16>(const __nv_bfloat16 *p
 }
 
 // ---------------------------------------------------------------------------
-// Host-side launchers (defined in bin.cu and blend.cu).
+// Host-side launchers (defined in bin.cu and blend.cu, for MaxV = 1 and kMaxViews).
 // ---------------------------------------------------------------------------
-cudaError_t launch_project_count(const Frame &F, const Workspace &W, long long n, const float *pos,
+template <int MaxV>
+cudaError_t launch_project_count(const Batch<MaxV> &B, const Workspace &W, long long n, const float *pos,
                                  const float *size_w, float4 *rec, cudaStream_t stream);
-cudaError_t launch_scan_fill(const Frame &F, const Workspace &W, long long n, const float4 *rec,
+template <int MaxV>
+cudaError_t launch_scan_fill(const Batch<MaxV> &B, const Workspace &W, long long n, const float4 *rec,
                              const float *opacity, cudaStream_t stream);
-cudaError_t launch_blend(const Frame &F, const Workspace &W, const void *desc, int desc_dtype, float *pyramid,
-                         unsigned *kept, unsigned char *n_kept, float *t_final, unsigned *n_frag,
+template <int MaxV>
+cudaError_t launch_blend(const Batch<MaxV> &B, const Workspace &W, const void *desc, int desc_dtype,
+                         float *pyramid, unsigned *kept, unsigned char *n_kept, float *t_final, unsigned *n_frag,
                          cudaStream_t stream);
-size_t tile_smem_bytes(const Frame &F, bool backward);
-cudaError_t launch_backward(const Frame &F, const Workspace &W, long long n, const float4 *rec,
+template <int MaxV>
+cudaError_t launch_backward(const Batch<MaxV> &B, const Workspace &W, long long n, const float4 *rec,
                             const float *opacity, const void *desc, int desc_dtype, const unsigned *kept,
                             const unsigned char *n_kept, const float *grad_pyramid, float *grad_pos,
                             float *grad_sw, float *grad_opacity, float *grad_desc, cudaStream_t stream);
+size_t tile_smem_bytes(const Frame &F, bool backward);
 
 }  // namespace tpk

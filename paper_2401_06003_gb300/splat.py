@@ -194,3 +194,198 @@ class TripsSplat(torch.autograd.Function):
 def splat(pos, size_w, opacity, desc, renderer: Renderer) -> torch.Tensor:
     """Differentiable trilinear point splatting into a [P, D] feature pyramid."""
     return TripsSplat.apply(pos, size_w, opacity, desc, renderer)
+
+
+class BatchRenderer:
+    """Several cameras rendered from one point cloud by the same launches.
+
+    Each camera may have its own resolution and screen tile shape (``tiles``,
+    one (tile_w, tile_h) per view, e.g. from :func:`autotune_tiles`).  The
+    views' pyramids are concatenated in view order; ``view_offsets[v]`` is the
+    first row of view v.  Gradients are those of the sum of the views' losses.
+    """
+
+    def __init__(self, cameras, n_layers: int, K: int = 16, D: int = 4, eps: float = 0.25,
+                 desc_dtype=torch.float32, mode: str = "recompute", tiles=None, device=None):
+        self.lib = _lib.load()
+        self.cameras = list(cameras)
+        V = len(self.cameras)
+        if not 1 <= V <= 16:
+            raise ValueError("a batch holds 1 to 16 views")
+        self.n_views = V
+        self.cams = (_lib.tp_camera * V)(*[_lib.make_camera(c) for c in self.cameras])
+        self.set_tiles(tiles)
+        if desc_dtype not in _DTYPES:
+            raise ValueError(f"descriptor dtype {desc_dtype} not supported")
+        self.desc_dtype = desc_dtype
+        self.mode = {"store": _lib.TP_STORE_LISTS, "recompute": _lib.TP_RECOMPUTE}[mode]
+        self.cfg = _lib.make_config(n_layers, K, D, eps, _DTYPES[desc_dtype], self.mode)
+        self.n_layers, self.K, self.D = int(n_layers), int(K), int(D)
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        offs = (ctypes.c_int64 * (V + 1))()
+        P = self.lib.tp_batch_pixels(self.cams, V, n_layers, offs)
+        if P < 0:
+            raise ValueError("invalid cameras or layer count")
+        self.P = int(P)
+        self.view_offsets = [int(v) for v in offs]
+
+    def set_tiles(self, tiles):
+        if tiles is None:
+            self.tiles = None
+            self._tiles_c = None
+        else:
+            tiles = [tuple(int(a) for a in t) for t in tiles]
+            if len(tiles) != self.n_views:
+                raise ValueError("one tile shape per view")
+            self.tiles = tiles
+            self._tiles_c = (ctypes.c_int32 * (2 * self.n_views))(*[a for t in tiles for a in t])
+
+    def _common(self):
+        return ctypes.byref(self.cfg), self.cams, self._tiles_c, self.n_views
+
+    def workspace_bytes(self, n: int, capacity: int = 0) -> int:
+        b = self.lib.tp_batch_workspace_bytes(*self._common(), int(n), int(capacity))
+        if b < 0:
+            raise ValueError("invalid configuration for the workspace")
+        return int(b)
+
+    def new_workspace(self, n: int, capacity: int = 0) -> torch.Tensor:
+        ws = torch.empty(self.workspace_bytes(n, capacity), dtype=torch.uint8, device=self.device)
+        assert ws.data_ptr() % 256 == 0
+        return ws
+
+    def view(self, pyramid: torch.Tensor, v: int) -> torch.Tensor:
+        """Rows of view v in a batched [P, ...] tensor."""
+        return pyramid[self.view_offsets[v]:self.view_offsets[v + 1]]
+
+    def project(self, pos, size_w, ws, records=None):
+        n = pos.shape[0]
+        _need(pos, torch.float32, (n, 3), "pos", self.device)
+        _need(size_w, torch.float32, (n,), "size_w", self.device)
+        if records is None:
+            records = torch.empty((self.n_views, n, 4), dtype=torch.float32, device=self.device)
+        st = self.lib.tp_batch_project(*self._common(), n, _ptr(pos), _ptr(size_w), _ptr(records), _ptr(ws),
+                                       ws.numel(), _stream(self.device))
+        _lib.check("tp_batch_project", st)
+        return records
+
+    def splat_forward(self, records, opacity, ws):
+        n = records.shape[1]
+        _need(opacity, torch.float32, (n,), "opacity", self.device)
+        st = self.lib.tp_batch_splat_forward(*self._common(), n, _ptr(records), _ptr(opacity), _ptr(ws), ws.numel(),
+                                             _stream(self.device))
+        _lib.check("tp_batch_splat_forward", st)
+
+    def blend(self, n, desc, ws, store_lists=False, stats=False, pyramid=None):
+        _need(desc, self.desc_dtype, (n, self.D), "desc", self.device)
+        dev = self.device
+        if pyramid is None:
+            pyramid = torch.empty((self.P, self.D), dtype=torch.float32, device=dev)
+        kept = n_kept = t_final = n_frag = None
+        if store_lists or stats:
+            kept = torch.empty((self.P, self.K), dtype=torch.int32, device=dev)
+            n_kept = torch.empty((self.P,), dtype=torch.uint8, device=dev)
+        if stats:
+            t_final = torch.empty((self.P,), dtype=torch.float32, device=dev)
+            n_frag = torch.empty((self.P,), dtype=torch.int32, device=dev)
+        st = self.lib.tp_batch_blend(*self._common(), n, _ptr(desc), _ptr(pyramid), _ptr(kept), _ptr(n_kept),
+                                     _ptr(t_final), _ptr(n_frag), _ptr(ws), ws.numel(), _stream(dev))
+        _lib.check("tp_batch_blend", st)
+        return pyramid, kept, n_kept, t_final, n_frag
+
+    def splat_backward(self, records, opacity, desc, grad_pyramid, ws, kept=None, n_kept=None, grads=None):
+        n = records.shape[1]
+        dev = self.device
+        _need(grad_pyramid, torch.float32, (self.P, self.D), "grad_pyramid", dev)
+        if grads is None:
+            grads = (torch.empty((n, 3), dtype=torch.float32, device=dev),
+                     torch.empty((n,), dtype=torch.float32, device=dev),
+                     torch.empty((n,), dtype=torch.float32, device=dev),
+                     torch.empty((n, self.D), dtype=torch.float32, device=dev))
+        gp, gs, go, gd = grads
+        st = self.lib.tp_batch_splat_backward(*self._common(), n, _ptr(records), _ptr(opacity), _ptr(desc),
+                                              _ptr(kept), _ptr(n_kept), _ptr(grad_pyramid), _ptr(gp), _ptr(gs),
+                                              _ptr(go), _ptr(gd), _ptr(ws), ws.numel(), _stream(dev))
+        _lib.check("tp_batch_splat_backward", st)
+        return grads
+
+    def status(self, ws) -> int:
+        flags = ctypes.c_int32(0)
+        st = self.lib.tp_get_status(_ptr(ws), _stream(self.device), ctypes.byref(flags))
+        if st == _lib.TP_ERR_CUDA or st == _lib.TP_ERR_INVALID_ARG:
+            _lib.check("tp_get_status", st)
+        return int(flags.value)
+
+    def render(self, pos, size_w, opacity, desc, store_lists=None, stats=False, ws=None) -> Frame:
+        n = pos.shape[0]
+        if store_lists is None:
+            store_lists = self.mode == _lib.TP_STORE_LISTS
+        if ws is None:
+            ws = self.new_workspace(n)
+        records = self.project(pos, size_w, ws)
+        self.splat_forward(records, opacity, ws)
+        pyramid, kept, n_kept, t_final, n_frag = self.blend(n, desc, ws, store_lists, stats)
+        return Frame(pyramid, records, ws, kept, n_kept, t_final, n_frag)
+
+    def backward(self, frame: Frame, opacity, desc, grad_pyramid):
+        use_lists = self.mode == _lib.TP_STORE_LISTS and frame.kept is not None
+        return self.splat_backward(frame.records, opacity, desc, grad_pyramid.contiguous(), frame.workspace,
+                                   frame.kept if use_lists else None, frame.n_kept if use_lists else None)
+
+
+TILE_CANDIDATES = ((16, 8), (16, 16), (32, 8), (8, 16), (8, 8))
+
+
+def autotune_tiles(cameras, n_layers, pos, size_w, opacity, desc, K=16, candidates=TILE_CANDIDATES, iters=3,
+                   desc_dtype=torch.float32, device=None):
+    """Per view, the screen tile shape with the fastest forward + backward.
+
+    Every candidate renders the view alone (project, splat, blend, backward
+    with a fixed upstream gradient) for ``iters`` timed iterations after one
+    warm-up; the shape with the lowest median time wins.  Views of equal
+    resolution are tuned once.  Returns (tiles, timings) where timings maps
+    (width, height) to {tile: ms}.
+    """
+    n = pos.shape[0]
+    D = desc.shape[1]
+    best, timings = {}, {}
+    for cam in cameras:
+        res = (int(cam.width), int(cam.height))
+        if res in best:
+            continue
+        times = {}
+        for tile in candidates:
+            try:
+                r = Renderer(cam, n_layers, K=K, D=D, desc_dtype=desc_dtype, mode="recompute", tile=tile,
+                             device=device)
+                ws = r.new_workspace(n)
+            except (ValueError, _lib.TripsError):
+                continue
+            G = torch.ones((r.P, D), dtype=torch.float32, device=r.device)
+            rec = torch.empty((n, 4), dtype=torch.float32, device=r.device)
+            pyr = torch.empty((r.P, D), dtype=torch.float32, device=r.device)
+            grads = (torch.empty((n, 3), device=r.device), torch.empty((n,), device=r.device),
+                     torch.empty((n,), device=r.device), torch.empty((n, D), device=r.device))
+            ms = []
+            try:
+                for it in range(iters + 1):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    r.project(pos, size_w, ws, records=rec)
+                    r.splat_forward(rec, opacity, ws)
+                    r.blend(n, desc, ws, pyramid=pyr)
+                    r.splat_backward(rec, opacity, desc, G, ws, grads=grads)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    if it > 0:
+                        ms.append(e0.elapsed_time(e1))
+            except _lib.TripsError:
+                continue
+            times[tile] = sorted(ms)[len(ms) // 2]
+            del ws, G, rec, pyr, grads
+        if not times:
+            raise RuntimeError(f"no tile shape works for {res}")
+        best[res] = min(times, key=times.get)
+        timings[res] = times
+    return [best[(int(c.width), int(c.height))] for c in cameras], timings
