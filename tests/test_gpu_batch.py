@@ -105,8 +105,8 @@ def test_batch_step_replays_as_one_cuda_graph(scene):
         graph.replay()
         torch.cuda.synchronize()
         assert torch.equal(pyr, eager[0])
-        for a, b in zip(grads, eager[1:]):
-            assert_close_scaled(a.cpu().numpy().reshape(n, -1), b.cpu().numpy().reshape(n, -1), 1e-5,
+        for a, b in zip(grads, eager[1:]):  # same arithmetic; only the order of the float atomics differs
+            assert_close_scaled(a.cpu().numpy().reshape(n, -1), b.cpu().numpy().reshape(n, -1), 1e-4,
                                 name="replayed gradients")
 
 
