@@ -258,6 +258,44 @@ TP_API tp_status tp_batch_splat_backward(const tp_config *cfg, const tp_camera *
                                          float *grad_opacity, float *grad_desc, void *ws, int64_t ws_bytes,
                                          tp_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Forward render with no caller workspace.  The paper has no counterpart:
+ * this entry point exists for callers that may not allocate device memory
+ * at run time, such as a plug-in inside a host application that owns every
+ * CUDA allocation through its own pool, or a real-time frame loop that must
+ * not call cudaMalloc (which can synchronise the whole device) once it runs.
+ *
+ * It enqueues the same kernels as tp_project, tp_splat_forward and tp_blend
+ * (without kept lists or statistics) on `stream`, but keeps the frame's
+ * workspace in an array that the library reserves in device memory: a fixed
+ * TP_STATIC_WORKSPACE_BYTES on every GPU that loads the library, held until
+ * the process exits.  The call itself allocates and frees nothing.
+ *
+ *   records [n][4] (device, 16-byte aligned): written as by tp_project.
+ *   pyramid [P][D] (device): written as by tp_blend.
+ *   device_flags (device, nullable): if not NULL, one uint32 that receives
+ *     the frame's TP_FLAG_* bits (stream-ordered; no host synchronisation).
+ *
+ * - Returns TP_ERR_CAPACITY, before enqueuing anything, when the frame's
+ *   workspace, tp_workspace_bytes(cfg, cam, n, 0), is larger than
+ *   TP_STATIC_WORKSPACE_BYTES: about 190 bytes per point plus 8 per pyramid
+ *   pixel, so some 340 thousand points at 256 x 256 with 4 layers and 200
+ *   thousand at 1920 x 1080 with 8 layers.
+ * - The first call on a device, with that device current, looks up the
+ *   array's device address once; make that first call before any stream
+ *   capture begins (for instance once at start-up).
+ * - Every call on a device uses the same array, and each call starts by
+ *   resetting the parts that must begin at zero.  Calls that can run at the
+ *   same time on the GPU (unordered streams, several host threads) race on
+ *   the array and corrupt each other's results: order them on one stream.
+ * ------------------------------------------------------------------------ */
+#define TP_STATIC_WORKSPACE_BYTES ((int64_t)64 << 20)
+
+TP_API tp_status tp_render_forward_static(const tp_config *cfg, const tp_camera *cam, int64_t n, const float *pos,
+                                          const float *size_w, const float *opacity, const void *desc,
+                                          float *records, float *pyramid, uint32_t *device_flags,
+                                          tp_stream_t stream);
+
 /*
  * Synchronises `stream` and reads the workspace's device status word into
  * *device_flags (host; TP_FLAG_* bits).  Returns TP_ERR_CAPACITY,
