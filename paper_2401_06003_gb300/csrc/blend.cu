@@ -213,10 +213,6 @@ struct TopK {
     }
 };
 
-// Small tile lists (at most one entry per thread) are merged without the
-// chunk machinery; each pixel remembers up to kSmallCap covering entries.
-constexpr int kSmallCap = 32;
-
 // Builds the kept list of the thread's pixel (thread t owns pixel t of the
 // tile, t < tile_px); returns the kept count, *nfrag gets the candidates.
 template <int K>
