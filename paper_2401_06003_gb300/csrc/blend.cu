@@ -498,12 +498,13 @@ __global__ void k_tile_backward(const __grid_constant__ Batch<MaxV> B, Workspace
     if (beg > end) beg = end;
     for (unsigned e = beg + tid; e < end; e += NT) {
         const unsigned long long key = W.bucket_key[e];
-        entry_taps(F, g, W.bucket_pay[e], [&](int px) {
+        entry_taps_w(F, g, W.bucket_pay[e], [&](int px, float gam) {
             if (key <= thr[px]) {
                 const unsigned q = atomicAdd(S.cnt + px, 1u);
                 if (q < (unsigned)K) {
                     kk[q * TP + px] = key;
                     ke[q * TP + px] = e;
+                    kt[q * TP + px] = gam;
                 }
             }
         });
@@ -513,21 +514,30 @@ __global__ void k_tile_backward(const __grid_constant__ Batch<MaxV> B, Workspace
     int nk = (int)S.cnt[tid];
     if (nk > K) nk = K;
     if (nk == 0) return;
-    // sort the pixel's slots (at most K) by key
+    // sort the pixel's slots (at most K) by key, carrying the slot index
     TopK<K> top;
     top.clear();
-    for (int q = 0; q < nk; ++q) top.insert_short(kk[q * TP + tid], ke[q * TP + tid]);
+    for (int q = 0; q < nk; ++q) top.insert_short(kk[q * TP + tid], (unsigned)q);
+    // front to back: each kept fragment's entry and T_m, from the opacity the
+    // rebuild left in its slot (no global loads)
+    float Tm[K];
+    float T = 1.0f;
+#pragma unroll
+    for (int m = 0; m < K; ++m) {
+        Tm[m] = 0.0f;
+        if (m < nk) {
+            const unsigned q = top.e[m];
+            const float gam = kt[q * TP + tid];
+            top.e[m] = ke[q * TP + tid];
+            Tm[m] = T;
+            T = T * (1.0f - gam);
+        }
+    }
 #pragma unroll
     for (int m = 0; m < K; ++m) {
         kk[m * TP + tid] = top.key[m];
         ke[m * TP + tid] = top.e[m];
-    }
-    float T = 1.0f;
-    for (int m = 0; m < nk; ++m) {
-        const float4 pay = W.bucket_pay[ke[m * TP + tid]];
-        const FragW w = frag_weights(F, pay.x, pay.y, pay.z, L, j, k);
-        kt[m * TP + tid] = T;
-        T = T * (1.0f - w.wx * w.wy * w.iota * pay.w);
+        kt[m * TP + tid] = Tm[m];
     }
     float G[kMaxGradD];
     for (int d = 0; d < D; ++d) G[d] = __ldg(grad_pyr + pix * D + d);
