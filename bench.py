@@ -401,7 +401,7 @@ def run_ours(args):
 def run_batch(args):
     import torch
 
-    from paper_2401_06003_gb300 import BatchRenderer, Renderer, autotune_tiles, scenes
+    from paper_2401_06003_gb300 import BatchRenderer, Renderer, autotune_batch_tiles, scenes
     from paper_2401_06003_gb300.build import build as build_lib
 
     build_lib()
@@ -414,7 +414,7 @@ def run_batch(args):
     op = torch.from_numpy(sc.opacity).to(dev)
     desc = torch.from_numpy(sc.desc).to(dev)
     t0 = time.perf_counter()
-    tiles, tuning = autotune_tiles(sc.cameras, sc.n_layers, pos, sw, op, desc, K=sc.K, device=dev)
+    tiles, tuning = autotune_batch_tiles(sc.cameras, sc.n_layers, pos, sw, op, desc, K=sc.K, device=dev)
     tune_s = time.perf_counter() - t0
     br = BatchRenderer(sc.cameras, sc.n_layers, K=sc.K, D=D, tiles=tiles, device=dev)
     ws = br.new_workspace(N)

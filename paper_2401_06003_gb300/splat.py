@@ -389,3 +389,84 @@ def autotune_tiles(cameras, n_layers, pos, size_w, opacity, desc, K=16, candidat
         best[res] = min(times, key=times.get)
         timings[res] = times
     return [best[(int(c.width), int(c.height))] for c in cameras], timings
+
+
+def autotune_batch_tiles(cameras, n_layers, pos, size_w, opacity, desc, K=16, candidates=TILE_CANDIDATES, iters=3,
+                         desc_dtype=torch.float32, device=None, start=None):
+    """Screen tile shapes for a batch of views, tuned on the batch itself.
+
+    A batch launch runs every tile CTA with the block of the batch's largest
+    tile, so the shape that is fastest for a view rendered alone can slow the
+    other views of the batch down.  Starting from ``start`` (default: 16 x 8
+    for every view), each resolution in turn tries every candidate while the
+    other resolutions keep their current shape, timing the whole batch step
+    (project, splat, blend, backward with a fixed upstream gradient; median of
+    ``iters`` after one warm-up), and keeps the fastest.  Returns (tiles,
+    timings) where timings maps (width, height) to {tile: ms of the batch}.
+    """
+    cameras = list(cameras)
+    n = pos.shape[0]
+    D = desc.shape[1]
+    res_of = [(int(c.width), int(c.height)) for c in cameras]
+    groups = list(dict.fromkeys(res_of))
+    current = dict(zip(res_of, start)) if start is not None else {r: (16, 8) for r in groups}
+    buf = [None]
+
+    def batch_ms(choice):
+        tiles = [choice[r] for r in res_of]
+        try:
+            br = BatchRenderer(cameras, n_layers, K=K, D=D, desc_dtype=desc_dtype, mode="recompute", tiles=tiles,
+                               device=device)
+            need = br.workspace_bytes(n)
+        except (ValueError, _lib.TripsError):
+            return None
+        if buf[0] is None or buf[0].numel() < need:
+            buf[0] = None
+            buf[0] = torch.empty(need, dtype=torch.uint8, device=br.device)
+        ws = buf[0][:need]
+        V = br.n_views
+        G = torch.ones((br.P, D), dtype=torch.float32, device=br.device)
+        rec = torch.empty((V, n, 4), dtype=torch.float32, device=br.device)
+        pyr = torch.empty((br.P, D), dtype=torch.float32, device=br.device)
+        grads = (torch.empty((n, 3), device=br.device), torch.empty((n,), device=br.device),
+                 torch.empty((n,), device=br.device), torch.empty((n, D), device=br.device))
+        ms = []
+        try:
+            for it in range(iters + 1):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                br.project(pos, size_w, ws, records=rec)
+                br.splat_forward(rec, opacity, ws)
+                br.blend(n, desc, ws, pyramid=pyr)
+                br.splat_backward(rec, opacity, desc, G, ws, grads=grads)
+                e1.record()
+                torch.cuda.synchronize()
+                if it > 0:
+                    ms.append(e0.elapsed_time(e1))
+        except _lib.TripsError:
+            return None
+        return sorted(ms)[len(ms) // 2]
+
+    timings = {}
+    best_ms = batch_ms(current)
+    if best_ms is None:
+        raise RuntimeError("the starting tile shapes do not work for this batch")
+    for res in groups:
+        times = {current[res]: best_ms}
+        for tile in candidates:
+            tile = tuple(int(a) for a in tile)
+            if tile in times:
+                continue
+            trial = dict(current)
+            trial[res] = tile
+            ms = batch_ms(trial)
+            if ms is None:
+                continue
+            times[tile] = ms
+        pick = min(times, key=times.get)
+        current[res] = pick
+        best_ms = times[pick]
+        timings[res] = times
+    buf[0] = None
+    return [current[r] for r in res_of], timings

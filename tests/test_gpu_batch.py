@@ -6,7 +6,7 @@ import torch
 
 import oracle
 from gpu_helpers import GRAD_RTOL, assert_close_scaled, compare_forward, compare_records, device, to_dev
-from paper_2401_06003_gb300 import BatchRenderer, Renderer, autotune_tiles, scenes
+from paper_2401_06003_gb300 import BatchRenderer, Renderer, autotune_batch_tiles, autotune_tiles, scenes
 
 pytestmark = pytest.mark.gpu
 
@@ -141,3 +141,21 @@ def test_orbit16_full_size_sampled():
                    t_final=br.view(fb.t_final, v).cpu().numpy(), n_frag=br.view(fb.n_frag, v).cpu().numpy())
         off, _, _ = oracle.pyramid_layout(sc.cameras[v].width, sc.cameras[v].height, sc.n_layers)
         compare_forward(out, ofr.render(), off.tolist(), rows=rows, name=f"orbit view {v}")
+
+
+def test_batch_autotune_times_the_batch(scene):
+    cams = _cams()
+    pos, sw, op, desc = _inputs(scene)
+    tiles, timings = autotune_batch_tiles(cams, 4, pos, sw, op, desc, candidates=((16, 8), (8, 8), (32, 32)),
+                                          iters=2, device=device())
+    assert len(tiles) == len(cams)
+    for cam, t in zip(cams, tiles):
+        res = (cam.width, cam.height)
+        assert t in timings[res] and t != (32, 32)  # the oversized tile is refused, never timed
+        assert timings[res][t] == min(timings[res].values())
+    # the chosen shapes render the batch exactly as the single views do
+    br = BatchRenderer(cams, 4, K=8, D=4, tiles=tiles, mode="store", device=device())
+    fb = br.render(pos, sw, op, desc)
+    for v, cam in enumerate(cams):
+        fs = Renderer(cam, 4, K=8, D=4, tile=tiles[v], mode="store", device=device()).render(pos, sw, op, desc)
+        assert torch.equal(br.view(fb.pyramid, v), fs.pyramid)
