@@ -370,6 +370,24 @@ def run_ours(args):
     fwd_ms = max_over_ranks(f0.elapsed_time(f1), world, dev) / args.steps
     flags = r.status(ws)
 
+    # camera adjoint of the same frame (one pass over the points' gradients;
+    # not part of the step): records, positions and point gradients read once
+    cam_out = torch.empty(16, dtype=torch.float64, device=dev)
+    r.camera_backward(pos, rec, grads[0], grads[1], out=cam_out)
+    torch.cuda.synchronize(dev)
+    c0 = torch.cuda.Event(enable_timing=True)
+    c1 = torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    for _ in range(args.steps):
+        r.camera_backward(pos, rec, grads[0], grads[1], out=cam_out)
+    c1.record(stream)
+    torch.cuda.synchronize(dev)
+    cam_ms = max_over_ranks(c0.elapsed_time(c1), world, dev) / args.steps
+    cam_bytes = 44 * N + 16 * 8
+    camera = {"ms": round(cam_ms, 4), "algorithmic_bytes": cam_bytes,
+              "achieved_gbs": round(cam_bytes / (cam_ms * 1e-3) / 1e9, 1),
+              "frac": round(cam_bytes / (cam_ms * 1e-3) / 1e9 / peak, 4)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(sc, args.cpu_frames)
@@ -384,11 +402,12 @@ def run_ours(args):
                        "height": sc.camera.height, "layers": sc.n_layers, "K": sc.K, "D": D,
                        "desc_dtype": "bf16" if b == 2 else "f32",
                        "mode": args.mode, "tile": args.tile, "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2 (216 MB of point inputs per step); no flush"},
+                       "l2": f"inputs larger than L2 ({(20 + b * D) * N / 1e6:.0f} MB of point inputs per step); "
+                             "no flush"},
             "forward_ms": round(fwd_ms, 4), "fwd_bwd_ms": round(ms_per_step, 4),
             "forward_mpoints_s": round(N / (fwd_ms * 1e-3) / 1e6, 3),
             "counters": {"N": N, "V": V, "F": F, "Fk": Fk, "P": P},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "camera_backward": camera, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": KERNELS_PER_STEP * args.steps, "clocks": clk, "device_flags": flags,
         }
         print(json.dumps(line), flush=True)

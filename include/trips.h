@@ -22,6 +22,8 @@
  *                     front to back (Sec. 3.2, Eq. 6-7; Sec. 3.6)
  *   tp_splat_backward gradients of a loss with respect to positions, world
  *                     sizes, opacities and descriptors (Sec. 3.5, Sec. 3.6)
+ *   tp_camera_backward the gradient with respect to the camera intrinsics and
+ *                     pose, from one view's point gradients (Sec. 3.5)
  *
  * Conventions shared by every call
  * --------------------------------
@@ -214,6 +216,29 @@ TP_API tp_status tp_splat_backward(const tp_config *cfg, const tp_camera *cam, i
                             const float *opacity, const void *desc, const uint32_t *kept, const uint8_t *n_kept,
                             const float *grad_pyramid, float *grad_pos, float *grad_size_w, float *grad_opacity,
                             float *grad_desc, void *ws, int64_t ws_bytes, tp_stream_t stream);
+
+/*
+ * Camera adjoint (the paper optimises camera poses and intrinsics along with
+ * the points: Sec. 3 pipeline figure, Sec. 3.5).  The camera enters only
+ * through each point's screen position and size (Eq. 2), so its gradient
+ * follows from the point gradients of one view's backward pass:
+ *   dL/dX_c = (R^T)^-1 grad_pos,  Gx = dL/dX_c[0] Z_c/fx,  Gy = dL/dX_c[1] Z_c/fy,
+ *   Gs = grad_size_w Z_c/fx  (the point's summed dL/dx, dL/dy, dL/ds);
+ *   dL/dfx = sum Gx (x-cx)/fx + Gs s/fx,  dL/dfy = sum Gy (y-cy)/fy,
+ *   dL/dcx = sum Gx,  dL/dcy = sum Gy,  dL/dt = sum dL/dX_c,
+ *   dL/dR[r][c] = sum dL/dX_c[r] X_w[c]   (sums over the visible points).
+ *   pos [n][3], records [n][4] (this view's tp_project output, 16-byte
+ *   aligned), grad_pos [n][3], grad_size_w [n]: device, read.  The point
+ *   gradients must come from a backward pass of this view alone (the batched
+ *   backward sums the views' gradients).
+ *   grad_camera [16] (device, float64, overwritten): dL/d(fx, fy, cx, cy,
+ *   R[0..8] row-major, t[0..2]) -- the order of tp_camera's fields.
+ * R must be invertible (TP_ERR_INVALID_ARG otherwise); for a rotation
+ * (R^T)^-1 = R.
+ */
+TP_API tp_status tp_camera_backward(const tp_camera *cam, int64_t n, const float *pos, const float *records,
+                                    const float *grad_pos, const float *grad_size_w, double *grad_camera,
+                                    tp_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * Batches of views.  Up to TP_MAX_VIEWS cameras (each with its own

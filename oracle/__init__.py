@@ -14,6 +14,7 @@ Parity status per function (what pins each one is in ``tests/test_oracle*``):
   fragment lists / K cap / order          pinned (brute force on tiny inputs)
   blending                                pinned (closed forms, brute force)
   adjoint                                 pinned (central finite differences)
+  camera adjoint                          pinned (central finite differences of the camera)
 """
 from __future__ import annotations
 
@@ -66,6 +67,7 @@ def _load():
         lib.orc_frame_fragments.argtypes = [P, P, P, P, P]
         lib.orc_frame_render.argtypes = [P, P, P, P, P, P]
         lib.orc_frame_backward.argtypes = [P, P, P, P, P, P, P]
+        lib.orc_frame_camera_backward.argtypes = [P, P, P]
         lib.orc_frame_fd.restype = ctypes.c_int
         lib.orc_frame_fd.argtypes = [P, P, i64, P, dbl, dbl, dbl, dbl, P, P]
         del i32
@@ -184,6 +186,13 @@ class Frame:
         )
         self._lib.orc_frame_backward(self._h, _ptr(G), _ptr(out["pos"]), _ptr(out["size_w"]),
                                      _ptr(out["opacity"]), _ptr(out["desc"]), _ptr(out["screen"]))
+        return out
+
+    def camera_backward(self, G):
+        """dL/d(fx, fy, cx, cy, R[0..8], t[0..2]) of sum(G * C) over the frame's pixels [16]."""
+        G = np.ascontiguousarray(G, np.float64).reshape(self.n_pix, self.D)
+        out = np.zeros(16, np.float64)
+        self._lib.orc_frame_camera_backward(self._h, _ptr(G), _ptr(out))
         return out
 
     def finite_differences(self, G, points, h_pos=1e-6, h_sw_rel=1e-6, h_alpha=1e-6, h_desc=1e-3):

@@ -17,7 +17,8 @@
  *   - front-to-back alpha blending C = sum_m T_m alpha_m c_m   (Eq. 6-7)
  *   - the adjoint of all of the above with respect to positions, world
  *     sizes, opacities and descriptors (the paper optimises all of them,
- *     Sec. 3.5 and Sec. 3.6 "the sorted per-pixel lists are stored").
+ *     Sec. 3.5 and Sec. 3.6 "the sorted per-pixel lists are stored"), and
+ *     with respect to the camera intrinsics and pose (Sec. 3.5).
  *
  * The oracle is the plain definition: enumerate every fragment of every
  * point, sort the complete list of every pixel by (depth, point index), keep
@@ -637,6 +638,63 @@ void orc_frame_backward(const oframe *fr, const double *G, double *grad_pos, dou
         if (grad_pos) { grad_pos[3 * i] = gp[0]; grad_pos[3 * i + 1] = gp[1]; grad_pos[3 * i + 2] = gp[2]; }
         if (grad_sw) grad_sw[i] = gw;
         if (grad_screen) { grad_screen[3 * i] = gx[i]; grad_screen[3 * i + 1] = gy[i]; grad_screen[3 * i + 2] = gs[i]; }
+    }
+    free(gx); free(gy); free(gs);
+}
+
+/*
+ * Gradient of L = sum over the frame's pixels of G . C with respect to the
+ * camera (the paper optimises camera poses and intrinsics along with the
+ * points: Sec. 3 pipeline figure, Sec. 3.5).  The camera enters only through
+ * each point's screen position and size (Eq. 2):
+ *   X_c = R X_w + t,  x = fx X_c/Z_c + cx,  y = fy Y_c/Z_c + cy,  s = fx s_w/Z_c,
+ * so with the point's screen-space gradient (gx, gy, gs) from the pixel
+ * adjoints, by the chain rule:
+ *   dL/dfx = gx X_c/Z_c + gs s_w/Z_c,   dL/dfy = gy Y_c/Z_c,
+ *   dL/dcx = gx,   dL/dcy = gy,
+ *   dL/dX_c = (gx fx/Z_c, gy fy/Z_c, -(gx fx X_c + gy fy Y_c + gs fx s_w)/Z_c^2),
+ *   dL/dt = dL/dX_c,   dL/dR[r][c] = dL/dX_c[r] X_w[c],
+ * summed over the visible points.  X_c/Z_c, Y_c/Z_c and s_w/Z_c are read off
+ * the frame's screen state: (x - cx)/fx, (y - cy)/fy, s/fx.  Depth order and
+ * layer choice are piecewise constant and carry no gradient.
+ * out16 = dL/d(fx, fy, cx, cy, R[0..8] row-major, t[0..2]); overwritten.
+ */
+void orc_frame_camera_backward(const oframe *fr, const double *G, double *out16)
+{
+    int64_t n = fr->n;
+    int D = fr->D;
+    const float *c = fr->cam.f;
+    double fx = c[0], fy = c[1], cx = c[2], cy = c[3];
+    double *gx = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double *gy = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    double *gs = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    for (int q = 0; q < 16; ++q) out16[q] = 0.0;
+    for (int64_t s = 0; s < fr->n_pix; ++s) {
+        const okey *list = fr->keys + fr->pix_start[s];
+        int64_t cnt = fr->pix_start[s + 1] - fr->pix_start[s];
+        if (cnt == 0) continue;
+        pixel_adjoint(fr, list, cnt, G + s * D, NULL, NULL, gx, gy, gs);
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        const oproj *o = &fr->proj[i];
+        if (!o->vis) continue;
+        double Zc = o->z;
+        double xn = (o->x - cx) / fx; /* X_c / Z_c */
+        double yn = (o->y - cy) / fy; /* Y_c / Z_c */
+        double sn = o->s / fx;        /* s_w / Z_c */
+        out16[0] += gx[i] * xn + gs[i] * sn;
+        out16[1] += gy[i] * yn;
+        out16[2] += gx[i];
+        out16[3] += gy[i];
+        double dXc[3];
+        dXc[0] = gx[i] * fx / Zc;
+        dXc[1] = gy[i] * fy / Zc;
+        dXc[2] = -(gx[i] * fx * xn + gy[i] * fy * yn + gs[i] * fx * sn) / Zc;
+        const float *Xw = fr->pos + 3 * i;
+        for (int r = 0; r < 3; ++r) {
+            for (int col = 0; col < 3; ++col) out16[4 + 3 * r + col] += dXc[r] * (double)Xw[col];
+            out16[13 + r] += dXc[r];
+        }
     }
     free(gx); free(gy); free(gs);
 }

@@ -143,6 +143,21 @@ class Renderer:
         _lib.check("tp_splat_backward", st)
         return grads
 
+    def camera_backward(self, pos, records, grad_pos, grad_size_w, out=None) -> torch.Tensor:
+        """dL/d(fx, fy, cx, cy, R[0..8], t[0..2]) [16] float64, from this view's point gradients."""
+        n = pos.shape[0]
+        dev = self.device
+        _need(pos, torch.float32, (n, 3), "pos", dev)
+        _need(records, torch.float32, (n, 4), "records", dev)
+        _need(grad_pos, torch.float32, (n, 3), "grad_pos", dev)
+        _need(grad_size_w, torch.float32, (n,), "grad_size_w", dev)
+        if out is None:
+            out = torch.empty(16, dtype=torch.float64, device=dev)
+        st = self.lib.tp_camera_backward(ctypes.byref(self.cam), n, _ptr(pos), _ptr(records), _ptr(grad_pos),
+                                         _ptr(grad_size_w), _ptr(out), _stream(dev))
+        _lib.check("tp_camera_backward", st)
+        return out
+
     def status(self, ws) -> int:
         """Synchronises the current stream and returns the TP_FLAG_* bits of the frame."""
         flags = ctypes.c_int32(0)

@@ -382,3 +382,78 @@ def test_float32_frame_adjoint_matches_anchored_differences():
     assert valid.mean() > 0.9
     err = np.abs(ad - fd)[valid]
     assert err.max() <= 1e-6 * np.abs(fd[valid]).max(), err.max()
+
+
+# --------------------------------------------------------------------------
+# Camera adjoint against central finite differences of the camera
+# --------------------------------------------------------------------------
+
+def _rotation(ax, ay, az):
+    cx, sx, cy, sy, cz, sz = math.cos(ax), math.sin(ax), math.cos(ay), math.sin(ay), math.cos(az), math.sin(az)
+    Rx = np.array([[1, 0, 0], [0, cx, -sx], [0, sx, cx]])
+    Ry = np.array([[cy, 0, sy], [0, 1, 0], [-sy, 0, cy]])
+    Rz = np.array([[cz, -sz, 0], [sz, cz, 0], [0, 0, 1]])
+    return Rz @ Ry @ Rx
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_camera_adjoint_matches_camera_differences(seed):
+    """dL/d(fx, fy, cx, cy, R, t) against central differences of the whole
+    float64 frame in each camera parameter.  The perturbed parameters are
+    float32 values; the difference quotient divides by their actual spacing.
+    A parameter whose perturbation changes any fragment list (a tap, a layer
+    or an order) is skipped: there the frame is not differentiable."""
+    rng = np.random.default_rng(300 + seed)
+    n, W, H, n_layers, K, D = 120, 48, 36, 4, 4, 3
+    pos = np.stack([rng.uniform(-0.8, 0.8, n), rng.uniform(-0.6, 0.6, n), rng.uniform(-0.8, 0.8, n)], 1)
+    pos = pos.astype(np.float32)
+    sw = np.exp(rng.uniform(math.log(3e-3), math.log(0.3), n)).astype(np.float32)
+    alpha = rng.uniform(0.1, 0.95, n).astype(np.float32)
+    desc = rng.uniform(-1, 1, (n, D)).astype(np.float32)
+    R = _rotation(*rng.uniform(-0.3, 0.3, 3))
+    cam = _cam(40.0, W, H, R=R, t=(0.05, -0.1, 3.0))
+    cam[1] = 44.0  # fy != fx
+    cam[2], cam[3] = 23.5, 18.25
+
+    def frame(c):
+        return oracle.Frame(c, W, H, n_layers, K, pos, sw, alpha, desc, prec32=False)
+
+    fr = frame(cam)
+    G = rng.uniform(-1, 1, (fr.n_pix, D))
+    g = fr.camera_backward(G)
+    pix0, _, idx0, _ = fr.fragments()
+    steps = [1e-5 * abs(float(cam[q])) for q in range(4)] + [1e-6] * 12
+    fd = np.full(16, np.nan)
+    for q in range(16):
+        cp, cm = cam.copy(), cam.copy()
+        cp[q] = np.float32(float(cam[q]) + steps[q])
+        cm[q] = np.float32(float(cam[q]) - steps[q])
+        fp, fm = frame(cp), frame(cm)
+        same = True
+        for f_ in (fp, fm):
+            pix, _, idx, _ = f_.fragments()
+            same = same and pix.shape == pix0.shape and (pix == pix0).all() and (idx == idx0).all()
+        if not same:
+            continue
+        Lp = float((G * fp.render()["pyramid"]).sum())
+        Lm = float((G * fm.render()["pyramid"]).sum())
+        fd[q] = (Lp - Lm) / (float(cp[q]) - float(cm[q]))
+    ok = ~np.isnan(fd)
+    assert ok.sum() >= 12, ok
+    for sl in (slice(0, 4), slice(4, 13), slice(13, 16)):  # intrinsics, rotation, translation
+        m = ok[sl]
+        if not m.any():
+            continue
+        ref, got = fd[sl][m], g[sl][m]
+        scale = np.abs(fd[sl][m]).max()
+        assert np.all(np.abs(got - ref) <= 1e-4 * (np.abs(ref) + 1e-3 * scale)), (sl, got, ref)
+    assert np.abs(g).max() > 0
+
+
+def test_camera_adjoint_zero_without_visible_points():
+    """Points behind the camera carry no camera gradient."""
+    n, W, H = 10, 16, 12
+    pos = np.stack([np.zeros(n), np.zeros(n), -np.linspace(1, 2, n)], 1).astype(np.float32)
+    fr = oracle.Frame(_cam(10.0, W, H), W, H, 2, 4, pos, np.full(n, 0.1, np.float32), np.full(n, 0.5, np.float32),
+                      np.ones((n, 2), np.float32), prec32=False)
+    assert np.all(fr.camera_backward(np.ones((fr.n_pix, 2))) == 0)
