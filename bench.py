@@ -388,6 +388,33 @@ def run_ours(args):
               "achieved_gbs": round(cam_bytes / (cam_ms * 1e-3) / 1e9, 1),
               "frac": round(cam_bytes / (cam_ms * 1e-3) / 1e9 / peak, 4)}
 
+    # pyramid merge of the frame into one image, and its adjoint (not part of the step)
+    P0 = r.layer_offsets[1]
+    Plast = P - r.layer_offsets[-2]
+    merged = torch.empty((P, D), device=dev)
+    g_img = (torch.rand((P0, D), generator=gen, device=dev) * 2 - 1).contiguous()
+    g_pyr = torch.empty((P, D), device=dev)
+    r.merge(pyr, out=merged)
+    r.merge_backward(g_img, out=g_pyr)
+    torch.cuda.synchronize(dev)
+    m0, m1, m2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    m0.record(stream)
+    for _ in range(args.steps):
+        r.merge(pyr, out=merged)
+    m1.record(stream)
+    for _ in range(args.steps):
+        r.merge_backward(g_img, out=g_pyr)
+    m2.record(stream)
+    torch.cuda.synchronize(dev)
+    mf_ms = max_over_ranks(m0.elapsed_time(m1), world, dev) / args.steps
+    mb_ms = max_over_ranks(m1.elapsed_time(m2), world, dev) / args.steps
+    mf_bytes = 4 * D * (3 * P - P0)       # read P, write M, read each coarser merged layer once
+    mb_bytes = 4 * D * (P0 + 2 * P - Plast)  # copy the image gradient, read each finer layer, write each layer
+    merge = {"launches": sc.n_layers, "ms": round(mf_ms, 4), "algorithmic_bytes": mf_bytes,
+             "frac": round(mf_bytes / (mf_ms * 1e-3) / 1e9 / peak, 4),
+             "backward_ms": round(mb_ms, 4), "backward_algorithmic_bytes": mb_bytes,
+             "backward_frac": round(mb_bytes / (mb_ms * 1e-3) / 1e9 / peak, 4)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(sc, args.cpu_frames)
@@ -407,7 +434,8 @@ def run_ours(args):
             "forward_ms": round(fwd_ms, 4), "fwd_bwd_ms": round(ms_per_step, 4),
             "forward_mpoints_s": round(N / (fwd_ms * 1e-3) / 1e6, 3),
             "counters": {"N": N, "V": V, "F": F, "Fk": Fk, "P": P},
-            "roofline": roofline, "camera_backward": camera, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "camera_backward": camera, "pyramid_merge": merge, "cpu_baseline": cpu,
+            "e2e": e2e,
             "gpu_launches": KERNELS_PER_STEP * args.steps, "clocks": clk, "device_flags": flags,
         }
         print(json.dumps(line), flush=True)

@@ -24,6 +24,9 @@
  *                     sizes, opacities and descriptors (Sec. 3.5, Sec. 3.6)
  *   tp_camera_backward the gradient with respect to the camera intrinsics and
  *                     pose, from one view's point gradients (Sec. 3.5)
+ *   tp_merge          the decoder's layer merge in its weight-free form: the
+ *                     pyramid summed into one image by bilinear upsampling
+ *                     (Sec. 3.3), and tp_merge_backward, its adjoint
  *
  * Conventions shared by every call
  * --------------------------------
@@ -239,6 +242,29 @@ TP_API tp_status tp_splat_backward(const tp_config *cfg, const tp_camera *cam, i
 TP_API tp_status tp_camera_backward(const tp_camera *cam, int64_t n, const float *pos, const float *records,
                                     const float *grad_pos, const float *grad_size_w, double *grad_camera,
                                     tp_stream_t stream);
+
+/*
+ * Pyramid merge (the decoder's layer merge, Sec. 3.3: every layer but the
+ * finest is upsampled bilinearly and merged with the next finer one), in its
+ * fixed form without trained weights -- a sum:
+ *   M_{n-1} = P_{n-1},   M_L = P_L + up2(M_{L+1}),
+ * where up2 samples layer L+1 at the centres of layer L's pixels: pixel j of
+ * layer L reads layer L+1 at r = max((j + 0.5)/2 - 0.5, 0) with taps
+ * floor(r), min(floor(r) + 1, W_{L+1} - 1) and weights 1 - (r - floor r),
+ * r - floor r (the same along y).
+ *   pyramid [P][D] (device, read), merged [P][D] (device, written): merged
+ *   layer L is M_L in the pyramid layout, so rows [0, W H) are the merged
+ *   full-resolution image.  merged may be the pyramid itself (in place).
+ * tp_merge_backward: from dL/d(image) grad_image [W H][D] (device), writes
+ *   grad_pyramid [P][D] = dL/dP (dL/dP_L = dL/dM_L, dL/dM_{L+1} =
+ *   up2^T dL/dM_L).  grad_image may be grad_pyramid's first rows.
+ * 1 <= D <= 64; one kernel launch per layer.
+ */
+TP_API tp_status tp_merge(const tp_camera *cam, int32_t n_layers, int32_t D, const float *pyramid, float *merged,
+                          tp_stream_t stream);
+
+TP_API tp_status tp_merge_backward(const tp_camera *cam, int32_t n_layers, int32_t D, const float *grad_image,
+                                   float *grad_pyramid, tp_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * Batches of views.  Up to TP_MAX_VIEWS cameras (each with its own

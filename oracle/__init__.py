@@ -15,6 +15,8 @@ Parity status per function (what pins each one is in ``tests/test_oracle*``):
   blending                                pinned (closed forms, brute force)
   adjoint                                 pinned (central finite differences)
   camera adjoint                          pinned (central finite differences of the camera)
+  pyramid merge and its adjoint           pinned (torch bilinear interpolation, closed
+                                          forms, dot-product test)
 """
 from __future__ import annotations
 
@@ -211,3 +213,74 @@ class Frame:
         if rc != 0:
             raise RuntimeError(f"oracle finite differences failed ({rc})")
         return fd, valid.astype(bool)
+
+
+# ---------------------------------------------------------------------------
+# Pyramid merge: the fixed (weight-free) form of the decoder's layer merge
+# (Sec. 3.3: every layer but the finest is upsampled bilinearly and merged
+# with the next finer one).  Merging is a sum:
+#   M_{n-1} = P_{n-1},   M_L = P_L + up2(M_{L+1}),
+# and up2 samples layer L+1 at the layer-L pixel centres: pixel j of layer L
+# sits at (j + 0.5) 2^L, i.e. at r = (j + 0.5)/2 - 0.5 in layer L+1 units,
+# clamped to r >= 0; taps x0 = floor(r) and min(x0 + 1, W_{L+1} - 1) with
+# weights 1 - (r - x0) and r - x0.  M_0 is the merged full-resolution image.
+# ---------------------------------------------------------------------------
+
+def _up2_axis(n_out, n_in):
+    r = np.maximum((np.arange(n_out, dtype=np.float64) + 0.5) / 2.0 - 0.5, 0.0)
+    x0 = np.floor(r).astype(np.int64)
+    x1 = np.minimum(x0 + 1, n_in - 1)
+    return x0, x1, r - x0
+
+
+def upsample2(C, H, W):
+    """Bilinear x2 upsampling of C [Hc, Wc, D] to [H, W, D] (H <= 2 Hc, W <= 2 Wc)."""
+    C = np.asarray(C, np.float64)
+    y0, y1, ly = _up2_axis(H, C.shape[0])
+    x0, x1, lx = _up2_axis(W, C.shape[1])
+    lx = lx[None, :, None]
+    top = C[y0][:, x0] * (1.0 - lx) + C[y0][:, x1] * lx
+    bot = C[y1][:, x0] * (1.0 - lx) + C[y1][:, x1] * lx
+    return top * (1.0 - ly)[:, None, None] + bot * ly[:, None, None]
+
+
+def upsample2_adjoint(G, Hc, Wc):
+    """Transpose of upsample2: G [H, W, D] -> [Hc, Wc, D]."""
+    G = np.asarray(G, np.float64)
+    H, W, D = G.shape
+    y0, y1, ly = _up2_axis(H, Hc)
+    x0, x1, lx = _up2_axis(W, Wc)
+    out = np.zeros((Hc, Wc, D), np.float64)
+    for yy, wy in ((y0, 1.0 - ly), (y1, ly)):
+        for xx, wx in ((x0, 1.0 - lx), (x1, lx)):
+            np.add.at(out, (yy[:, None], xx[None, :]), G * (wy[:, None] * wx[None, :])[:, :, None])
+    return out
+
+
+def merge_pyramid(pyramid, width, height, n_layers):
+    """Merged layers M [P, D] in the pyramid's layout; rows [0, W H) are the image."""
+    off, ws, hs = pyramid_layout(width, height, n_layers)
+    P = np.asarray(pyramid, np.float64)
+    D = P.shape[1]
+    M = np.zeros_like(P)
+    for L in range(n_layers - 1, -1, -1):
+        layer = P[off[L]:off[L + 1]].reshape(hs[L], ws[L], D)
+        if L < n_layers - 1:
+            coarse = M[off[L + 1]:off[L + 2]].reshape(hs[L + 1], ws[L + 1], D)
+            layer = layer + upsample2(coarse, hs[L], ws[L])
+        M[off[L]:off[L + 1]] = layer.reshape(-1, D)
+    return M
+
+
+def merge_pyramid_backward(grad_image, width, height, n_layers):
+    """dL/dP [P, D] from dL/d(image) [W H, D]: dL/dP_L = dL/dM_L, dL/dM_{L+1} = up2^T dL/dM_L."""
+    off, ws, hs = pyramid_layout(width, height, n_layers)
+    g = np.asarray(grad_image, np.float64)
+    D = g.shape[1]
+    out = np.zeros((int(off[-1]), D), np.float64)
+    gm = g.reshape(hs[0], ws[0], D)
+    for L in range(n_layers):
+        out[off[L]:off[L + 1]] = gm.reshape(-1, D)
+        if L + 1 < n_layers:
+            gm = upsample2_adjoint(gm, hs[L + 1], ws[L + 1])
+    return out

@@ -158,6 +158,27 @@ class Renderer:
         _lib.check("tp_camera_backward", st)
         return out
 
+    def merge(self, pyramid, out=None) -> torch.Tensor:
+        """Merged layers [P, D] (the decoder's weight-free merge); rows [0, W H) are the image."""
+        dev = self.device
+        _need(pyramid, torch.float32, (self.P, self.D), "pyramid", dev)
+        if out is None:
+            out = torch.empty((self.P, self.D), dtype=torch.float32, device=dev)
+        st = self.lib.tp_merge(ctypes.byref(self.cam), self.n_layers, self.D, _ptr(pyramid), _ptr(out), _stream(dev))
+        _lib.check("tp_merge", st)
+        return out
+
+    def merge_backward(self, grad_image, out=None) -> torch.Tensor:
+        """dL/dpyramid [P, D] from dL/d(merged image) [W H, D]."""
+        dev = self.device
+        _need(grad_image, torch.float32, (self.camera.width * self.camera.height, self.D), "grad_image", dev)
+        if out is None:
+            out = torch.empty((self.P, self.D), dtype=torch.float32, device=dev)
+        st = self.lib.tp_merge_backward(ctypes.byref(self.cam), self.n_layers, self.D, _ptr(grad_image), _ptr(out),
+                                        _stream(dev))
+        _lib.check("tp_merge_backward", st)
+        return out
+
     def status(self, ws) -> int:
         """Synchronises the current stream and returns the TP_FLAG_* bits of the frame."""
         flags = ctypes.c_int32(0)
