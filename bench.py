@@ -410,6 +410,24 @@ def run_ours(args):
     mb_ms = max_over_ranks(m1.elapsed_time(m2), world, dev) / args.steps
     mf_bytes = 4 * D * (3 * P - P0)       # read P, write M, read each coarser merged layer once
     mb_bytes = 4 * D * (P0 + 2 * P - Plast)  # copy the image gradient, read each finer layer, write each layer
+    # point-size initialisation of the cloud (exact 4-NN mean distance; not part of the step)
+    from paper_2401_06003_gb300 import init_point_sizes
+    sizes0 = torch.empty(N, device=dev)
+    kws = torch.empty(int(r.lib.tp_init_sizes_workspace_bytes(N)), dtype=torch.uint8, device=dev)
+    init_point_sizes(pos, out=sizes0, ws=kws)
+    torch.cuda.synchronize(dev)
+    k0, k1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+    reps = max(1, min(args.steps, 5))
+    k0.record(stream)
+    for _ in range(reps):
+        init_point_sizes(pos, out=sizes0, ws=kws)
+    k1.record(stream)
+    torch.cuda.synchronize(dev)
+    knn_ms = max_over_ranks(k0.elapsed_time(k1), world, dev) / reps
+    size_init = {"ms": round(knn_ms, 3), "mpoints_s": round(N / (knn_ms * 1e-3) / 1e6, 1), "k": 4,
+                 "workspace_mb": round(kws.numel() / 1e6, 1)}
+    del kws
+
     merge = {"launches": sc.n_layers, "ms": round(mf_ms, 4), "algorithmic_bytes": mf_bytes,
              "frac": round(mf_bytes / (mf_ms * 1e-3) / 1e9 / peak, 4),
              "backward_ms": round(mb_ms, 4), "backward_algorithmic_bytes": mb_bytes,
@@ -434,7 +452,8 @@ def run_ours(args):
             "forward_ms": round(fwd_ms, 4), "fwd_bwd_ms": round(ms_per_step, 4),
             "forward_mpoints_s": round(N / (fwd_ms * 1e-3) / 1e6, 3),
             "counters": {"N": N, "V": V, "F": F, "Fk": Fk, "P": P},
-            "roofline": roofline, "camera_backward": camera, "pyramid_merge": merge, "cpu_baseline": cpu,
+            "roofline": roofline, "camera_backward": camera, "pyramid_merge": merge, "point_size_init": size_init,
+            "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": KERNELS_PER_STEP * args.steps, "clocks": clk, "device_flags": flags,
         }

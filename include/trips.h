@@ -24,6 +24,8 @@
  *                     sizes, opacities and descriptors (Sec. 3.5, Sec. 3.6)
  *   tp_camera_backward the gradient with respect to the camera intrinsics and
  *                     pose, from one view's point gradients (Sec. 3.5)
+ *   tp_init_point_sizes initial world sizes: mean distance to the 4 nearest
+ *                     neighbours (Sec. 3.6)
  *   tp_merge          the decoder's layer merge in its weight-free form: the
  *                     pyramid summed into one image by bilinear upsampling
  *                     (Sec. 3.3), and tp_merge_backward, its adjoint
@@ -265,6 +267,28 @@ TP_API tp_status tp_merge(const tp_camera *cam, int32_t n_layers, int32_t D, con
 
 TP_API tp_status tp_merge_backward(const tp_camera *cam, int32_t n_layers, int32_t D, const float *grad_image,
                                    float *grad_pyramid, tp_stream_t stream);
+
+/*
+ * Point-size initialisation (Sec. 3.6): size_w[i] = the mean distance from
+ * point i to its 4 nearest other points (exact, float32 distances).  A
+ * point's own index is never its neighbour; duplicates at distance 0 are.
+ * With fewer than 5 finite points the mean runs over the others (0 for one
+ * point); points with a non-finite coordinate are nobody's neighbour and get
+ * size 0.  Coordinates are expected below 1e18 in magnitude.
+ *   pos [n][3] (device, read), size_w [n] (device, written).
+ *   ws: device workspace of tp_init_sizes_workspace_bytes(n) bytes, 256-byte
+ *   aligned (about 32 n + 8 T bytes, T the power of two >= 2 n).
+ * Method: hashed uniform grids of cell c_m = c0 8^m, m = 0..5 (c0 = box
+ * extent / (8 max(64, 4 n^(1/3)))), each filled by a counting sort by a
+ * locality-preserving cell hash; each point searches rings of cells around
+ * its own until its 4th distance is within the searched radius, moving to
+ * the next coarser grid after 3 rings (the last grid covers the whole box).
+ * All on the device; no host synchronisation.
+ */
+TP_API int64_t tp_init_sizes_workspace_bytes(int64_t n_points);
+
+TP_API tp_status tp_init_point_sizes(int64_t n, const float *pos, float *size_w, void *ws, int64_t ws_bytes,
+                                     tp_stream_t stream);
 
 /* ------------------------------------------------------------------------
  * Batches of views.  Up to TP_MAX_VIEWS cameras (each with its own

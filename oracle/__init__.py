@@ -17,6 +17,7 @@ Parity status per function (what pins each one is in ``tests/test_oracle*``):
   camera adjoint                          pinned (central finite differences of the camera)
   pyramid merge and its adjoint           pinned (torch bilinear interpolation, closed
                                           forms, dot-product test)
+  point-size initialisation               pinned (brute force, lattice closed forms)
 """
 from __future__ import annotations
 
@@ -284,3 +285,42 @@ def merge_pyramid_backward(grad_image, width, height, n_layers):
         if L + 1 < n_layers:
             gm = upsample2_adjoint(gm, hs[L + 1], ws[L + 1])
     return out
+
+
+# ---------------------------------------------------------------------------
+# Point-size initialisation (Sec. 3.6): each point's initial world size is
+# the mean distance to its four nearest other points.  A point's own index is
+# never its neighbour; duplicates at distance 0 are.  With fewer than five
+# points the mean runs over the n - 1 others (0 for a single point).  Points
+# with a non-finite coordinate are nobody's neighbour and get size 0.
+# ---------------------------------------------------------------------------
+
+def init_point_sizes(pos, k=4, points=None):
+    """Mean distance to the k nearest other points, float64 (KD-tree query).
+
+    Returns sizes for every point, or for the indices in ``points`` only."""
+    from scipy.spatial import cKDTree
+
+    P = np.asarray(pos, np.float64)
+    n = P.shape[0]
+    sel = np.arange(n) if points is None else np.asarray(points, np.int64)
+    out = np.zeros(sel.size, np.float64)
+    ok = np.isfinite(P).all(axis=1)
+    idx = np.nonzero(ok)[0]
+    m = idx.size
+    if m < 2:
+        return out
+    kk = min(k, m - 1)
+    tree = cKDTree(P[idx])
+    local = np.full(n, -1, np.int64)
+    local[idx] = np.arange(m)
+    qsel = np.nonzero(ok[sel])[0]
+    dist, nb = tree.query(P[sel[qsel]], k=kk + 1)
+    dist = dist.reshape(qsel.size, kk + 1)
+    nb = nb.reshape(qsel.size, kk + 1)
+    for r, q in enumerate(qsel):
+        own = np.nonzero(nb[r] == local[sel[q]])[0]
+        keep = np.delete(dist[r], own[0] if own.size else kk)  # drop the point itself, else the farthest
+        out[q] = keep.mean()
+    return out
+

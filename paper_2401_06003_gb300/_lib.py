@@ -67,6 +67,8 @@ _SIGS = {
     "tp_batch_splat_backward": (ctypes.c_int, [ctypes.POINTER(tp_config), _P, _P, ctypes.c_int32, _I64, _P, _P, _P,
                                                _P, _P, _P, _P, _P, _P, _P, _P, _I64, _P]),
     "tp_camera_backward": (ctypes.c_int, [ctypes.POINTER(tp_camera), _I64, _P, _P, _P, _P, _P, _P]),
+    "tp_init_sizes_workspace_bytes": (_I64, [_I64]),
+    "tp_init_point_sizes": (ctypes.c_int, [_I64, _P, _P, _P, _I64, _P]),
     "tp_merge": (ctypes.c_int, [ctypes.POINTER(tp_camera), ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
     "tp_merge_backward": (ctypes.c_int, [ctypes.POINTER(tp_camera), ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
     "tp_render_forward_static": (ctypes.c_int, [ctypes.POINTER(tp_config), ctypes.POINTER(tp_camera), _I64, _P, _P,

@@ -506,3 +506,22 @@ def autotune_batch_tiles(cameras, n_layers, pos, size_w, opacity, desc, K=16, ca
         timings[res] = times
     buf[0] = None
     return [current[r] for r in res_of], timings
+
+
+def init_point_sizes(pos: torch.Tensor, out: torch.Tensor | None = None, ws: torch.Tensor | None = None):
+    """Initial world sizes [n]: mean distance to the 4 nearest other points (on the GPU)."""
+    lib = _lib.load()
+    if pos.dtype != torch.float32 or pos.dim() != 2 or pos.shape[1] != 3 or not pos.is_contiguous():
+        raise ValueError("pos: expected contiguous float32 [n, 3]")
+    n = pos.shape[0]
+    dev = pos.device
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=dev)
+    need = int(lib.tp_init_sizes_workspace_bytes(n))
+    if need < 0:
+        raise ValueError("too many points")
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+    st = lib.tp_init_point_sizes(n, _ptr(pos), _ptr(out), _ptr(ws), ws.numel(), _stream(dev))
+    _lib.check("tp_init_point_sizes", st)
+    return out
