@@ -71,10 +71,27 @@ __device__ __forceinline__ TileSmem carve(const Frame &F, unsigned char *base)
     return m;
 }
 
+// The backward keeps K slots per pixel (key, entry, T_m: 16 bytes a slot)
+// in its region, then the same counters.
+__host__ __device__ inline size_t backward_region_bytes(size_t NT, int K) { return align16((size_t)16 * K * NT); }
+
+__device__ __forceinline__ TileSmem carve_backward(int K, unsigned char *base)
+{
+    TileSmem m;
+    const size_t NT = blockDim.x;
+    m.ck = reinterpret_cast<unsigned long long *>(base);
+    m.ce = nullptr;
+    m.cnt = reinterpret_cast<unsigned *>(base + backward_region_bytes(NT, K));
+    m.off = m.cnt + NT;
+    m.cur = m.off + NT;
+    m.wsum = m.cur + NT;
+    return m;
+}
+
 size_t tile_smem_bytes(const Frame &F, bool backward)
 {
-    (void)backward;
-    return tile_region_bytes(F) + (3 * (size_t)F.tile_threads + 32) * sizeof(unsigned);
+    const size_t region = backward ? backward_region_bytes((size_t)F.tile_threads, F.K) : tile_region_bytes(F);
+    return region + (3 * (size_t)F.tile_threads + 32) * sizeof(unsigned);
 }
 
 // Exclusive scan of v over the CTA (blockDim.x <= 1024, a multiple of 32).
@@ -470,7 +487,8 @@ __device__ __forceinline__ void adjoint_fragment(const Frame &F, int L, int j, i
 // thread sorts its at most K slots, and runs the adjoint of its blend back to
 // front in a rolled loop.
 template <int K, typename DescT, int MaxV>
-__global__ void k_tile_backward(const __grid_constant__ Batch<MaxV> B, Workspace W, const DescT *__restrict__ desc,
+__global__ void k_tile_backward(const __grid_constant__ Batch<MaxV> B, Workspace W,
+                                                          const DescT *__restrict__ desc,
                                 const float *__restrict__ grad_pyr, float *__restrict__ gpos, float *__restrict__ gsw,
                                 float *__restrict__ gop, float *__restrict__ gdesc)
 {
@@ -478,7 +496,7 @@ __global__ void k_tile_backward(const __grid_constant__ Batch<MaxV> B, Workspace
     const int tile = blockIdx.x;  // global over the batch
     const int v = view_of_tile(B, tile);
     const Frame &F = B.view[v];
-    const TileSmem S = carve(F, smem_raw);
+    const TileSmem S = carve_backward(K, smem_raw);
     const TileGeom g = tile_geom(F, tile - B.tile_base[v]);
     const int TP = F.tile_px, tid = threadIdx.x, NT = blockDim.x, L = g.L, D = F.D;
     const int j = g.x0 + tid % F.tile_w, k = g.y0 + tid / F.tile_w;
@@ -674,7 +692,7 @@ static cudaError_t backward_impl(const Batch<MaxV> &B, const Workspace &W, long 
                                                                               grad_pyr, gpos, gsw, gop, gdesc);
         return cudaGetLastError();
     }
-    const size_t smem = batch_smem(B);
+    const size_t smem = backward_region_bytes((size_t)B.max_threads, K) + (3 * (size_t)B.max_threads + 32) * 4;
     cudaError_t e = prepare_tile_kernel(k_tile_backward<K, DescT, MaxV>, smem, B.max_threads);
     if (e != cudaSuccess) return e;
     k_tile_backward<K, DescT, MaxV><<<B.n_tiles, B.max_threads, smem, stream>>>(B, W, d, grad_pyr, gpos, gsw,
