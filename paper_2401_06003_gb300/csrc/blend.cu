@@ -46,6 +46,7 @@ struct TileSmem {
     unsigned *ce;                // [4 chunk] chunk fragment payloads
     unsigned *cnt, *off, *cur;   // [tile_threads]
     unsigned *wsum;              // [32]
+    unsigned long long *thr;     // [blockDim] a pixel's current K-th key (forward only)
 };
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
@@ -68,6 +69,7 @@ __device__ __forceinline__ TileSmem carve(const Frame &F, unsigned char *base)
     m.off = m.cnt + NT;
     m.cur = m.off + NT;
     m.wsum = m.cur + NT;
+    m.thr = reinterpret_cast<unsigned long long *>(m.wsum + 32);
     return m;
 }
 
@@ -91,7 +93,7 @@ __device__ __forceinline__ TileSmem carve_backward(int K, unsigned char *base)
 size_t tile_smem_bytes(const Frame &F, bool backward)
 {
     const size_t region = backward ? backward_region_bytes((size_t)F.tile_threads, F.K) : tile_region_bytes(F);
-    return region + (3 * (size_t)F.tile_threads + 32) * sizeof(unsigned);
+    return region + (3 * (size_t)F.tile_threads + 32) * sizeof(unsigned) + (backward ? 0 : 8 * (size_t)F.tile_threads);
 }
 
 // Exclusive scan of v over the CTA (blockDim.x <= 1024, a multiple of 32).
@@ -231,26 +233,45 @@ struct TopK {
 };
 
 // Builds the kept list of the thread's pixel (thread t owns pixel t of the
-// tile, t < tile_px); returns the kept count, *nfrag gets the candidates.
+// tile, t < tile_px); returns the kept count.  With count_all, *nfrag gets
+// the pixel's number of candidate fragments.
+//
+// A tile whose list spans several chunks keeps, per pixel, the current K-th
+// key after each chunk: a later fragment at or behind it cannot enter the
+// list, so the count and scatter passes of the next chunks drop it (fewer
+// shared-memory atomics, writes and merge steps on dense tiles).  The kept
+// list is the same either way.  Single-chunk tiles, and frames whose
+// candidate counts are asked for, skip the thresholds.
 template <int K>
 __device__ int build_topk(const Frame &F, const Workspace &W, int tile, const TileGeom &g, const TileSmem &S,
-                          TopK<K> &top, unsigned *nfrag)
+                          TopK<K> &top, bool count_all, unsigned *nfrag)
 {
     const int TP = F.tile_px, tid = threadIdx.x, NT = blockDim.x;
     const bool owner = tid < TP;
     top.clear();
     S.cnt[tid] = 0u;
     S.cur[tid] = 0u;
+    S.thr[tid] = kEmptyKey;
     unsigned end = W.tile_off[tile + 1];
     if (end > W.capacity) end = W.capacity;
     unsigned beg = W.tile_off[tile];
     if (beg > end) beg = end;
     unsigned nfr = 0;
+    const bool multi = !count_all && end - beg > (unsigned)F.chunk;
     __syncthreads();
     for (unsigned c0 = beg; c0 < end; c0 += (unsigned)F.chunk) {
         const unsigned c1 = min(end, c0 + (unsigned)F.chunk);
-        for (unsigned e = c0 + tid; e < c1; e += NT)
-            entry_taps(F, g, W.bucket_pay[e], [&](int px) { atomicAdd(S.cnt + px, 1u); });
+        if (multi) {
+            for (unsigned e = c0 + tid; e < c1; e += NT) {
+                const unsigned long long key = W.bucket_key[e];
+                entry_taps(F, g, W.bucket_pay[e], [&](int px) {
+                    if (key < S.thr[px]) atomicAdd(S.cnt + px, 1u);
+                });
+            }
+        } else {
+            for (unsigned e = c0 + tid; e < c1; e += NT)
+                entry_taps(F, g, W.bucket_pay[e], [&](int px) { atomicAdd(S.cnt + px, 1u); });
+        }
         __syncthreads();
         const unsigned my = S.cnt[tid];
         S.off[tid] = block_exclusive_scan(my, S.wsum);
@@ -259,15 +280,18 @@ __device__ int build_topk(const Frame &F, const Workspace &W, int tile, const Ti
             const unsigned long long key = W.bucket_key[e];
             const float4 pay = W.bucket_pay[e];
             entry_taps_w(F, g, pay, [&](int px, float gam) {
-                const unsigned q = S.off[px] + atomicAdd(S.cur + px, 1u);
-                S.ck[q] = key;
-                S.ce[q] = __float_as_uint(gam);
+                if (!multi || key < S.thr[px]) {
+                    const unsigned q = S.off[px] + atomicAdd(S.cur + px, 1u);
+                    S.ck[q] = key;
+                    S.ce[q] = __float_as_uint(gam);
+                }
             });
         }
         __syncthreads();
         if (owner) {
             const unsigned a = S.off[tid];
             for (unsigned q = a; q < a + my; ++q) top.insert(S.ck[q], S.ce[q]);
+            if (multi) S.thr[tid] = top.key[K - 1];
             nfr += my;
         }
         S.cnt[tid] = 0u;
@@ -275,7 +299,7 @@ __device__ int build_topk(const Frame &F, const Workspace &W, int tile, const Ti
         __syncthreads();
     }
     *nfrag = nfr;
-    return nfr < (unsigned)K ? (int)nfr : K;
+    return top.n;
 }
 
 // beta * iota of a point with payload (x, y, s, alpha) at layer-L pixel (j, k),
@@ -334,8 +358,14 @@ __device__ __forceinline__ DescGroup<DescT> load_group(const DescT *__restrict__
     return r;
 }
 
-template <int K, typename DescT, int MaxV>
-__global__ void k_tile_blend(const __grid_constant__ Batch<MaxV> B, Workspace W, const DescT *__restrict__ desc,
+// STATS: the frame's candidate counts are asked for (n_frag); a separate
+// instantiation, so the plain blend carries none of that state.  Registers
+// are capped at 96 for K <= 16 so that five 128-thread CTAs fit on an SM
+// (the uncapped build of some instantiations takes 104 and fits four: the
+// 4K bf16 blend was 14% slower); K = 32 needs its registers for the list.
+template <int K, typename DescT, int MaxV, bool STATS>
+__global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_blend(const __grid_constant__ Batch<MaxV> B, Workspace W,
+                                             const DescT *__restrict__ desc,
                              float *__restrict__ pyramid, unsigned *__restrict__ kept,
                              unsigned char *__restrict__ n_kept, float *__restrict__ t_final,
                              unsigned *__restrict__ n_frag)
@@ -348,7 +378,7 @@ __global__ void k_tile_blend(const __grid_constant__ Batch<MaxV> B, Workspace W,
     const TileGeom g = tile_geom(F, tile - B.tile_base[v]);
     TopK<K> top;
     unsigned nfr;
-    int nk = build_topk<K>(F, W, tile, g, S, top, &nfr);
+    int nk = build_topk<K>(F, W, tile, g, S, top, STATS, &nfr);
     const int TP = F.tile_px, tid = threadIdx.x, L = g.L;
     const int j = g.x0 + tid % F.tile_w, k = g.y0 + tid / F.tile_w;
     const bool active = tid < TP && j < F.lw[L] && k < F.lh[L];
@@ -422,7 +452,7 @@ __global__ void k_tile_blend(const __grid_constant__ Batch<MaxV> B, Workspace W,
     }
     if (n_kept) n_kept[pix] = (unsigned char)nk;
     if (t_final) t_final[pix] = T;
-    if (n_frag) n_frag[pix] = nfr;
+    if (STATS) n_frag[pix] = nfr;
 }
 
 constexpr int kMaxGradD = 64;
@@ -661,7 +691,7 @@ static size_t batch_smem(const Batch<MaxV> &B)
 {
     size_t region = 0;
     for (int v = 0; v < B.n_views; ++v) region = region > tile_region_bytes(B.view[v]) ? region : tile_region_bytes(B.view[v]);
-    return region + (3 * (size_t)B.max_threads + 32) * sizeof(unsigned);
+    return region + (3 * (size_t)B.max_threads + 32) * sizeof(unsigned) + 8 * (size_t)B.max_threads;
 }
 
 template <int K, typename DescT, int MaxV>
@@ -670,10 +700,17 @@ static cudaError_t blend_impl(const Batch<MaxV> &B, const Workspace &W, const vo
                               cudaStream_t stream)
 {
     const size_t smem = batch_smem(B);
-    cudaError_t e = prepare_tile_kernel(k_tile_blend<K, DescT, MaxV>, smem, B.max_threads);
-    if (e != cudaSuccess) return e;
-    k_tile_blend<K, DescT, MaxV><<<B.n_tiles, B.max_threads, smem, stream>>>(
-        B, W, static_cast<const DescT *>(desc), pyramid, kept, n_kept, t_final, n_frag);
+    if (n_frag) {
+        cudaError_t e = prepare_tile_kernel(k_tile_blend<K, DescT, MaxV, true>, smem, B.max_threads);
+        if (e != cudaSuccess) return e;
+        k_tile_blend<K, DescT, MaxV, true><<<B.n_tiles, B.max_threads, smem, stream>>>(
+            B, W, static_cast<const DescT *>(desc), pyramid, kept, n_kept, t_final, n_frag);
+    } else {
+        cudaError_t e = prepare_tile_kernel(k_tile_blend<K, DescT, MaxV, false>, smem, B.max_threads);
+        if (e != cudaSuccess) return e;
+        k_tile_blend<K, DescT, MaxV, false><<<B.n_tiles, B.max_threads, smem, stream>>>(
+            B, W, static_cast<const DescT *>(desc), pyramid, kept, n_kept, t_final, n_frag);
+    }
     return cudaGetLastError();
 }
 
