@@ -516,8 +516,10 @@ __device__ __forceinline__ void adjoint_fragment(const Frame &F, int L, int j, i
 // fragment into one of its pixel's K slots (no selection work), each pixel's
 // thread sorts its at most K slots, and runs the adjoint of its blend back to
 // front in a rolled loop.
+// Registers are capped at 96 for K <= 16 (five 128-thread CTAs per SM); the
+// kept slots are sorted in shared memory, so no register list is live.
 template <int K, typename DescT, int MaxV>
-__global__ void k_tile_backward(const __grid_constant__ Batch<MaxV> B, Workspace W,
+__global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_backward(const __grid_constant__ Batch<MaxV> B, Workspace W,
                                                           const DescT *__restrict__ desc,
                                 const float *__restrict__ grad_pyr, float *__restrict__ gpos, float *__restrict__ gsw,
                                 float *__restrict__ gop, float *__restrict__ gdesc)
@@ -562,30 +564,32 @@ __global__ void k_tile_backward(const __grid_constant__ Batch<MaxV> B, Workspace
     int nk = (int)S.cnt[tid];
     if (nk > K) nk = K;
     if (nk == 0) return;
-    // sort the pixel's slots (at most K) by key, carrying the slot index
-    TopK<K> top;
-    top.clear();
-    for (int q = 0; q < nk; ++q) top.insert_short(kk[q * TP + tid], (unsigned)q);
-    // front to back: each kept fragment's entry and T_m, from the opacity the
+    // insertion sort of the pixel's slots (at most K) by key, in its own
+    // shared-memory column (no registers held for the list)
+    for (int a = 1; a < nk; ++a) {
+        const unsigned long long key = kk[a * TP + tid];
+        const unsigned ent = ke[a * TP + tid];
+        const float gam = kt[a * TP + tid];
+        int b = a - 1;
+        while (b >= 0 && kk[b * TP + tid] > key) {
+            kk[(b + 1) * TP + tid] = kk[b * TP + tid];
+            ke[(b + 1) * TP + tid] = ke[b * TP + tid];
+            kt[(b + 1) * TP + tid] = kt[b * TP + tid];
+            --b;
+        }
+        kk[(b + 1) * TP + tid] = key;
+        ke[(b + 1) * TP + tid] = ent;
+        kt[(b + 1) * TP + tid] = gam;
+    }
+    // front to back: T_m in place of each kept fragment's opacity, which the
     // rebuild left in its slot (no global loads)
-    float Tm[K];
-    float T = 1.0f;
-#pragma unroll
-    for (int m = 0; m < K; ++m) {
-        Tm[m] = 0.0f;
-        if (m < nk) {
-            const unsigned q = top.e[m];
-            const float gam = kt[q * TP + tid];
-            top.e[m] = ke[q * TP + tid];
-            Tm[m] = T;
+    {
+        float T = 1.0f;
+        for (int m = 0; m < nk; ++m) {
+            const float gam = kt[m * TP + tid];
+            kt[m * TP + tid] = T;
             T = T * (1.0f - gam);
         }
-    }
-#pragma unroll
-    for (int m = 0; m < K; ++m) {
-        kk[m * TP + tid] = top.key[m];
-        ke[m * TP + tid] = top.e[m];
-        kt[m * TP + tid] = Tm[m];
     }
     float G[kMaxGradD];
     for (int d = 0; d < D; ++d) G[d] = __ldg(grad_pyr + pix * D + d);
