@@ -595,7 +595,7 @@ __global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_backward(const __grid_con
     for (int d = 0; d < D; ++d) G[d] = __ldg(grad_pyr + pix * D + d);
     // back to front, four slots at a time: the loads of a batch go out first
     float R = 0.0f;
-    constexpr int NB = 4;
+    constexpr int NB = sizeof(DescT) == 2 ? 2 : 4;  // bf16 groups hold 8 channels: fewer in flight
     for (int m1 = nk - 1; m1 >= 0; m1 -= NB) {
         unsigned long long key[NB];
         float4 pay[NB];
