@@ -466,19 +466,21 @@ __device__ __forceinline__ void atomic_add4(float *p, float4 v)
 // Adjoint of one kept fragment, given its forward quantities; scatters the
 // point gradients.  G is the pixel's dL/dC; R the running back-to-front term.
 // t0 holds the first channel group of the point's descriptor, loaded by the caller.
-template <typename DescT>
+// DC > 0: the descriptor width known at compile time (G stays in registers).
+template <typename DescT, int DC>
 __device__ __forceinline__ void adjoint_fragment(const Frame &F, int L, int j, int k, unsigned i, float x, float y,
                                                  float z, float s, float al, float Tm, const float *G, float &R,
                                                  const DescGroup<DescT> &t0, const DescT *__restrict__ desc,
                                                  float *__restrict__ gpos, float *__restrict__ gsw,
                                                  float *__restrict__ gop, float *__restrict__ gdesc)
 {
-    const int D = F.D;
+    const int D = DC > 0 ? DC : F.D;
     constexpr int NG = DescGroup<DescT>::G;
     const FragW w = frag_weights(F, x, y, s, L, j, k);
     const float beta = w.wx * w.wy;
     const float gam = beta * w.iota * al;
     float gdot = 0.0f;
+#pragma unroll
     for (int d0 = 0; d0 < D; d0 += NG) {
         const DescGroup<DescT> t = d0 == 0 ? t0 : load_group(desc, i, D, d0, F.desc_vec);
 #pragma unroll
@@ -490,6 +492,7 @@ __device__ __forceinline__ void adjoint_fragment(const Frame &F, int L, int j, i
     const float tg = Tm * gam;
     float *gd = gdesc + (long long)i * D;
     if (F.grad_vec) {
+#pragma unroll
         for (int d0 = 0; d0 < D; d0 += 4)
             atomic_add4(gd + d0, make_float4(tg * G[d0], tg * G[d0 + 1], tg * G[d0 + 2], tg * G[d0 + 3]));
     } else {
@@ -518,7 +521,7 @@ __device__ __forceinline__ void adjoint_fragment(const Frame &F, int L, int j, i
 // front in a rolled loop.
 // Registers are capped at 96 for K <= 16 (five 128-thread CTAs per SM); the
 // kept slots are sorted in shared memory, so no register list is live.
-template <int K, typename DescT, int MaxV>
+template <int K, typename DescT, int MaxV, int DC>
 __global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_backward(const __grid_constant__ Batch<MaxV> B, Workspace W,
                                                           const DescT *__restrict__ desc,
                                 const float *__restrict__ grad_pyr, float *__restrict__ gpos, float *__restrict__ gsw,
@@ -530,7 +533,7 @@ __global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_backward(const __grid_con
     const Frame &F = B.view[v];
     const TileSmem S = carve_backward(K, smem_raw);
     const TileGeom g = tile_geom(F, tile - B.tile_base[v]);
-    const int TP = F.tile_px, tid = threadIdx.x, NT = blockDim.x, L = g.L, D = F.D;
+    const int TP = F.tile_px, tid = threadIdx.x, NT = blockDim.x, L = g.L, D = DC > 0 ? DC : F.D;
     const int j = g.x0 + tid % F.tile_w, k = g.y0 + tid / F.tile_w;
     const bool active = tid < TP && j < F.lw[L] && k < F.lh[L];
     const long long pix = B.pix_base[v] + F.pix_base[L] + (long long)k * F.lw[L] + j;
@@ -591,8 +594,9 @@ __global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_backward(const __grid_con
             T = T * (1.0f - gam);
         }
     }
-    float G[kMaxGradD];
-    for (int d = 0; d < D; ++d) G[d] = __ldg(grad_pyr + pix * D + d);
+    float G[DC > 0 ? DC : kMaxGradD];
+#pragma unroll
+    for (int d = 0; d < (DC > 0 ? DC : D); ++d) G[d] = __ldg(grad_pyr + pix * D + d);
     // back to front, four slots at a time: the loads of a batch go out first
     float R = 0.0f;
     constexpr int NB = sizeof(DescT) == 2 ? 2 : 4;  // bf16 groups hold 8 channels: fewer in flight
@@ -611,7 +615,7 @@ __global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_backward(const __grid_con
         for (int u = 0; u < NB; ++u) {
             const int m = m1 - u;
             if (m < 0) break;
-            adjoint_fragment<DescT>(F, L, j, k, (unsigned)(key[u] & 0xFFFFFFFFull), pay[u].x, pay[u].y,
+            adjoint_fragment<DescT, DC>(F, L, j, k, (unsigned)(key[u] & 0xFFFFFFFFull), pay[u].x, pay[u].y,
                                     __uint_as_float((unsigned)(key[u] >> 32)), pay[u].z, pay[u].w, kt[m * TP + tid],
                                     G, R, t0[u], desc, gpos, gsw, gop, gdesc);
         }
@@ -665,7 +669,7 @@ __global__ void __launch_bounds__(kBlock) k_stored_backward(const __grid_constan
             if (m >= nk) continue;
             const unsigned i = kept[pix * K + m];
             const float4 r = rec[i];
-            adjoint_fragment<DescT>(F, L, j, k, i, r.x, r.y, r.z, r.w, __ldg(opacity + i), Tm[m], G, R,
+            adjoint_fragment<DescT, 0>(F, L, j, k, i, r.x, r.y, r.z, r.w, __ldg(opacity + i), Tm[m], G, R,
                                     load_group(desc, i, F.D, 0, F.desc_vec), desc, gpos, gsw, gop, gdesc);
         }
     }
@@ -718,6 +722,17 @@ static cudaError_t blend_impl(const Batch<MaxV> &B, const Workspace &W, const vo
     return cudaGetLastError();
 }
 
+template <int K, typename DescT, int MaxV, int DC>
+static cudaError_t backward_launch(const Batch<MaxV> &B, const Workspace &W, const DescT *d, const float *grad_pyr,
+                                   float *gpos, float *gsw, float *gop, float *gdesc, size_t smem, cudaStream_t stream)
+{
+    cudaError_t e = prepare_tile_kernel(k_tile_backward<K, DescT, MaxV, DC>, smem, B.max_threads);
+    if (e != cudaSuccess) return e;
+    k_tile_backward<K, DescT, MaxV, DC><<<B.n_tiles, B.max_threads, smem, stream>>>(B, W, d, grad_pyr, gpos, gsw,
+                                                                                     gop, gdesc);
+    return cudaGetLastError();
+}
+
 template <int K, typename DescT, int MaxV>
 static cudaError_t backward_impl(const Batch<MaxV> &B, const Workspace &W, long long n, const float4 *rec,
                                  const float *opacity, const void *desc, const unsigned *kept,
@@ -734,11 +749,13 @@ static cudaError_t backward_impl(const Batch<MaxV> &B, const Workspace &W, long 
         return cudaGetLastError();
     }
     const size_t smem = backward_region_bytes((size_t)B.max_threads, K) + (3 * (size_t)B.max_threads + 32) * 4;
-    cudaError_t e = prepare_tile_kernel(k_tile_backward<K, DescT, MaxV>, smem, B.max_threads);
-    if (e != cudaSuccess) return e;
-    k_tile_backward<K, DescT, MaxV><<<B.n_tiles, B.max_threads, smem, stream>>>(B, W, d, grad_pyr, gpos, gsw,
-                                                                                 gop, gdesc);
-    return cudaGetLastError();
+    // the common descriptor widths get compile-time instantiations (K = 16)
+    const int D = B.view[0].D;
+    if (K == 16 && D == 4) return backward_launch<K, DescT, MaxV, 4>(B, W, d, grad_pyr, gpos, gsw, gop, gdesc, smem,
+                                                                      stream);
+    if (K == 16 && D == 16)
+        return backward_launch<K, DescT, MaxV, 16>(B, W, d, grad_pyr, gpos, gsw, gop, gdesc, smem, stream);
+    return backward_launch<K, DescT, MaxV, 0>(B, W, d, grad_pyr, gpos, gsw, gop, gdesc, smem, stream);
 }
 
 #define TPK_DISPATCH_K(KVAL, ...)                                   \
