@@ -50,6 +50,8 @@ def parse_args():
     ap.add_argument("--ref-sample", type=int, default=2_000_000, help="points per reference-arm step")
     ap.add_argument("--cpu-frames", type=int, default=2, help="full oracle frames timed for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the camera-adjoint, pyramid-merge and point-size timings (profiling the step alone)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     return ap.parse_args()
@@ -176,9 +178,10 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel, workload):
+def ncu_traffic(kernel, workload, points):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken from the current kernel sources; else None."""
+    was taken from the current kernel sources on this workload and point
+    count; else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as fh:
@@ -188,7 +191,7 @@ def ncu_traffic(kernel, workload):
     if d.get("source_hash") != source_hash():
         return None
     k = d.get("kernels", {}).get(kernel)
-    if not k or k.get("workload") != workload:
+    if not k or k.get("workload") != workload or k.get("points") != points:
         return None
     return k.get("dram_bytes_per_launch")
 
@@ -311,7 +314,7 @@ def run_ours(args):
     roofline = {
         "bound": "hbm", "kernel": kname, "stage": dom, "achieved": round(achieved, 1), "peak": peak,
         "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-        "traffic": ncu_traffic(kname, args.workload),
+        "traffic": ncu_traffic(kname, args.workload, N),
         "algorithmic_bytes": int(A[dom]),
         "step": {"achieved": round(step_bytes / (ms_per_step * 1e-3) / 1e9, 1),
                  "frac": round(step_bytes / (ms_per_step * 1e-3) / 1e9 / peak, 4),
@@ -393,68 +396,70 @@ def run_ours(args):
     fwd_ms = max_over_ranks(f0.elapsed_time(f1), world, dev) / args.steps
     flags = r.status(ws)
 
-    # camera adjoint of the same frame (one pass over the points' gradients;
-    # not part of the step): records, positions and point gradients read once
-    cam_out = torch.empty(16, dtype=torch.float64, device=dev)
-    r.camera_backward(pos, rec, grads[0], grads[1], out=cam_out)
-    torch.cuda.synchronize(dev)
-    c0 = torch.cuda.Event(enable_timing=True)
-    c1 = torch.cuda.Event(enable_timing=True)
-    c0.record(stream)
-    for _ in range(args.steps):
+    camera = merge = size_init = None
+    if not args.no_extras:
+        # camera adjoint of the same frame (one pass over the points' gradients;
+        # not part of the step): records, positions and point gradients read once
+        cam_out = torch.empty(16, dtype=torch.float64, device=dev)
         r.camera_backward(pos, rec, grads[0], grads[1], out=cam_out)
-    c1.record(stream)
-    torch.cuda.synchronize(dev)
-    cam_ms = max_over_ranks(c0.elapsed_time(c1), world, dev) / args.steps
-    cam_bytes = 44 * N + 16 * 8
-    camera = {"ms": round(cam_ms, 4), "algorithmic_bytes": cam_bytes,
-              "achieved_gbs": round(cam_bytes / (cam_ms * 1e-3) / 1e9, 1),
-              "frac": round(cam_bytes / (cam_ms * 1e-3) / 1e9 / peak, 4)}
+        torch.cuda.synchronize(dev)
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(args.steps):
+            r.camera_backward(pos, rec, grads[0], grads[1], out=cam_out)
+        c1.record(stream)
+        torch.cuda.synchronize(dev)
+        cam_ms = max_over_ranks(c0.elapsed_time(c1), world, dev) / args.steps
+        cam_bytes = 44 * N + 16 * 8
+        camera = {"ms": round(cam_ms, 4), "algorithmic_bytes": cam_bytes,
+                  "achieved_gbs": round(cam_bytes / (cam_ms * 1e-3) / 1e9, 1),
+                  "frac": round(cam_bytes / (cam_ms * 1e-3) / 1e9 / peak, 4)}
 
-    # pyramid merge of the frame into one image, and its adjoint (not part of the step)
-    P0 = r.layer_offsets[1]
-    Plast = P - r.layer_offsets[-2]
-    merged = torch.empty((P, D), device=dev)
-    g_img = (torch.rand((P0, D), generator=gen, device=dev) * 2 - 1).contiguous()
-    g_pyr = torch.empty((P, D), device=dev)
-    r.merge(pyr, out=merged)
-    r.merge_backward(g_img, out=g_pyr)
-    torch.cuda.synchronize(dev)
-    m0, m1, m2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-    m0.record(stream)
-    for _ in range(args.steps):
+        # pyramid merge of the frame into one image, and its adjoint (not part of the step)
+        P0 = r.layer_offsets[1]
+        Plast = P - r.layer_offsets[-2]
+        merged = torch.empty((P, D), device=dev)
+        g_img = (torch.rand((P0, D), generator=gen, device=dev) * 2 - 1).contiguous()
+        g_pyr = torch.empty((P, D), device=dev)
         r.merge(pyr, out=merged)
-    m1.record(stream)
-    for _ in range(args.steps):
         r.merge_backward(g_img, out=g_pyr)
-    m2.record(stream)
-    torch.cuda.synchronize(dev)
-    mf_ms = max_over_ranks(m0.elapsed_time(m1), world, dev) / args.steps
-    mb_ms = max_over_ranks(m1.elapsed_time(m2), world, dev) / args.steps
-    mf_bytes = 4 * D * (3 * P - P0)       # read P, write M, read each coarser merged layer once
-    mb_bytes = 4 * D * (P0 + 2 * P - Plast)  # copy the image gradient, read each finer layer, write each layer
-    # point-size initialisation of the cloud (exact 4-NN mean distance; not part of the step)
-    from paper_2401_06003_gb300 import init_point_sizes
-    sizes0 = torch.empty(N, device=dev)
-    kws = torch.empty(int(r.lib.tp_init_sizes_workspace_bytes(N)), dtype=torch.uint8, device=dev)
-    init_point_sizes(pos, out=sizes0, ws=kws)
-    torch.cuda.synchronize(dev)
-    k0, k1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
-    reps = max(1, min(args.steps, 5))
-    k0.record(stream)
-    for _ in range(reps):
+        torch.cuda.synchronize(dev)
+        m0, m1, m2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        m0.record(stream)
+        for _ in range(args.steps):
+            r.merge(pyr, out=merged)
+        m1.record(stream)
+        for _ in range(args.steps):
+            r.merge_backward(g_img, out=g_pyr)
+        m2.record(stream)
+        torch.cuda.synchronize(dev)
+        mf_ms = max_over_ranks(m0.elapsed_time(m1), world, dev) / args.steps
+        mb_ms = max_over_ranks(m1.elapsed_time(m2), world, dev) / args.steps
+        mf_bytes = 4 * D * (3 * P - P0)       # read P, write M, read each coarser merged layer once
+        mb_bytes = 4 * D * (P0 + 2 * P - Plast)  # copy the image gradient, read each finer layer, write each layer
+        # point-size initialisation of the cloud (exact 4-NN mean distance; not part of the step)
+        from paper_2401_06003_gb300 import init_point_sizes
+        sizes0 = torch.empty(N, device=dev)
+        kws = torch.empty(int(r.lib.tp_init_sizes_workspace_bytes(N)), dtype=torch.uint8, device=dev)
         init_point_sizes(pos, out=sizes0, ws=kws)
-    k1.record(stream)
-    torch.cuda.synchronize(dev)
-    knn_ms = max_over_ranks(k0.elapsed_time(k1), world, dev) / reps
-    size_init = {"ms": round(knn_ms, 3), "mpoints_s": round(N / (knn_ms * 1e-3) / 1e6, 1), "k": 4,
-                 "workspace_mb": round(kws.numel() / 1e6, 1)}
-    del kws
+        torch.cuda.synchronize(dev)
+        k0, k1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+        reps = max(1, min(args.steps, 5))
+        k0.record(stream)
+        for _ in range(reps):
+            init_point_sizes(pos, out=sizes0, ws=kws)
+        k1.record(stream)
+        torch.cuda.synchronize(dev)
+        knn_ms = max_over_ranks(k0.elapsed_time(k1), world, dev) / reps
+        size_init = {"ms": round(knn_ms, 3), "mpoints_s": round(N / (knn_ms * 1e-3) / 1e6, 1), "k": 4,
+                     "workspace_mb": round(kws.numel() / 1e6, 1)}
+        del kws
 
-    merge = {"launches": sc.n_layers, "ms": round(mf_ms, 4), "algorithmic_bytes": mf_bytes,
-             "frac": round(mf_bytes / (mf_ms * 1e-3) / 1e9 / peak, 4),
-             "backward_ms": round(mb_ms, 4), "backward_algorithmic_bytes": mb_bytes,
-             "backward_frac": round(mb_bytes / (mb_ms * 1e-3) / 1e9 / peak, 4)}
+        merge = {"launches": sc.n_layers, "ms": round(mf_ms, 4), "algorithmic_bytes": mf_bytes,
+                 "frac": round(mf_bytes / (mf_ms * 1e-3) / 1e9 / peak, 4),
+                 "backward_ms": round(mb_ms, 4), "backward_algorithmic_bytes": mb_bytes,
+                 "backward_frac": round(mb_bytes / (mb_ms * 1e-3) / 1e9 / peak, 4)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
