@@ -750,11 +750,12 @@ static cudaError_t backward_impl(const Batch<MaxV> &B, const Workspace &W, long 
     }
     const size_t smem = backward_region_bytes((size_t)B.max_threads, K) + (3 * (size_t)B.max_threads + 32) * 4;
     // the common descriptor widths get compile-time instantiations (K = 16)
-    const int D = B.view[0].D;
-    if (K == 16 && D == 4) return backward_launch<K, DescT, MaxV, 4>(B, W, d, grad_pyr, gpos, gsw, gop, gdesc, smem,
-                                                                      stream);
-    if (K == 16 && D == 16)
-        return backward_launch<K, DescT, MaxV, 16>(B, W, d, grad_pyr, gpos, gsw, gop, gdesc, smem, stream);
+    if constexpr (K == 16) {
+        const int D = B.view[0].D;
+        if (D == 4) return backward_launch<K, DescT, MaxV, 4>(B, W, d, grad_pyr, gpos, gsw, gop, gdesc, smem, stream);
+        if (D == 16)
+            return backward_launch<K, DescT, MaxV, 16>(B, W, d, grad_pyr, gpos, gsw, gop, gdesc, smem, stream);
+    }
     return backward_launch<K, DescT, MaxV, 0>(B, W, d, grad_pyr, gpos, gsw, gop, gdesc, smem, stream);
 }
 
