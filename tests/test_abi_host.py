@@ -64,3 +64,19 @@ def test_workspace_bytes_and_checks(lib):
     st = lib.tp_splat_forward(ctypes.byref(cfg), ctypes.byref(cam), 10, None, None, None, 0, None)
     assert st == _lib.TP_ERR_INVALID_ARG
     assert lib.tp_status_string(_lib.TP_ERR_CAPACITY).decode().startswith("workspace")
+
+
+def test_size_limits_are_refused_on_the_host(lib):
+    """Documented maxima: n < 2^27 points, 16 layers, D <= 64, width and height <= 32768."""
+    cam = _lib.make_camera(scenes.make_config("cube20k_256", n=10).camera)
+    cfg = _lib.make_config(4, 16, 4)
+    assert lib.tp_workspace_bytes(ctypes.byref(cfg), ctypes.byref(cam), (1 << 27) - 1, 1) > 0
+    assert lib.tp_workspace_bytes(ctypes.byref(cfg), ctypes.byref(cam), 1 << 27, 1) == -1
+    assert lib.tp_workspace_bytes(ctypes.byref(_lib.make_config(16, 16, 4)), ctypes.byref(cam), 10, 0) > 0
+    assert lib.tp_workspace_bytes(ctypes.byref(_lib.make_config(17, 16, 4)), ctypes.byref(cam), 10, 0) == -1
+    assert lib.tp_workspace_bytes(ctypes.byref(_lib.make_config(4, 16, 64)), ctypes.byref(cam), 10, 0) > 0
+    assert lib.tp_workspace_bytes(ctypes.byref(_lib.make_config(4, 16, 65)), ctypes.byref(cam), 10, 0) == -1
+    wide = _lib.make_camera(scenes.camera_at((0, 0, -3), (0, 0, 0), 32768, 2))
+    assert lib.tp_workspace_bytes(ctypes.byref(cfg), ctypes.byref(wide), 10, 0) > 0
+    wide.width = 32769
+    assert lib.tp_workspace_bytes(ctypes.byref(cfg), ctypes.byref(wide), 10, 0) == -1
