@@ -170,11 +170,18 @@ def measured_hbm_peak():
 
 
 def source_hash():
+    """Hash of the kernel sources' code, comments and whitespace removed (so an
+    edited comment does not disown the recorded ncu counters)."""
+    import re
+
     h = hashlib.sha256()
     for p in sorted(glob.glob(os.path.join(ROOT, "paper_2401_06003_gb300", "csrc", "*"))):
-        with open(p, "rb") as fh:
-            h.update(os.path.basename(p).encode())
-            h.update(fh.read())
+        with open(p, encoding="utf-8") as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(os.path.basename(p).encode())
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -51,7 +51,8 @@ struct TileSmem {
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
-// Bytes of the fragment region (the backward reuses it for its kept lists).
+// Bytes of the blend's fragment region (one chunk: 8-byte key and 4-byte
+// payload for at most four fragments per entry).
 __host__ __device__ inline size_t tile_region_bytes(const Frame &F)
 {
     return align16((size_t)32 * F.chunk) + align16((size_t)16 * F.chunk);
@@ -537,7 +538,7 @@ __global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_backward(const __grid_con
     const int j = g.x0 + tid % F.tile_w, k = g.y0 + tid / F.tile_w;
     const bool active = tid < TP && j < F.lw[L] && k < F.lh[L];
     const long long pix = B.pix_base[v] + F.pix_base[L] + (long long)k * F.lw[L] + j;
-    // slot-major private slots in the chunk area: key [K][TP], entry [K][TP], T_m [K][TP]
+    // slot-major private slots in the backward's region: key [K][TP], entry [K][TP], T_m [K][TP]
     unsigned long long *kk = S.ck;
     unsigned *ke = reinterpret_cast<unsigned *>(S.ck + (size_t)K * TP);
     float *kt = reinterpret_cast<float *>(ke + (size_t)K * TP);
