@@ -169,20 +169,34 @@ def measured_hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def source_hash():
-    """Hash of the kernel sources' code, comments and whitespace removed (so an
-    edited comment does not disown the recorded ncu counters)."""
+def _code_hash(texts):
     import re
 
     h = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_2401_06003_gb300", "csrc", "*"))):
-        with open(p, encoding="utf-8") as fh:
-            text = fh.read()
+    for name, text in texts:
         text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
         text = re.sub(r"//[^\n]*", " ", text)
-        h.update(os.path.basename(p).encode())
+        h.update(name.encode())
         h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
+
+
+# the source files each profiled kernel is compiled from
+KERNEL_FILES = {"k_project_count": ("bin.cu", "common.cuh"), "k_fill": ("bin.cu", "common.cuh"),
+                "k_tile_blend": ("blend.cu", "common.cuh"), "k_tile_backward": ("blend.cu", "common.cuh")}
+
+
+def source_hash(files=None):
+    """Hash of the kernel sources' code (all of csrc/, or the named files),
+    comments and whitespace removed, so an edited comment does not disown the
+    recorded ncu counters."""
+    csrc = os.path.join(ROOT, "paper_2401_06003_gb300", "csrc")
+    paths = sorted(glob.glob(os.path.join(csrc, "*"))) if files is None else [os.path.join(csrc, f) for f in files]
+    texts = []
+    for p in paths:
+        with open(p, encoding="utf-8") as fh:
+            texts.append((os.path.basename(p), fh.read()))
+    return _code_hash(texts)
 
 
 def ncu_traffic(kernel, workload, points):
@@ -195,10 +209,10 @@ def ncu_traffic(kernel, workload, points):
             d = json.load(fh)
     except (OSError, ValueError):
         return None
-    if d.get("source_hash") != source_hash():
-        return None
     k = d.get("kernels", {}).get(kernel)
     if not k or k.get("workload") != workload or k.get("points") != points:
+        return None
+    if k.get("source_hash") != source_hash(KERNEL_FILES.get(kernel)):
         return None
     return k.get("dram_bytes_per_launch")
 

@@ -83,46 +83,66 @@ __global__ void __launch_bounds__(kBlock) k_tile_totals(int n_tiles, Workspace W
     if (lane == 31) W.tile_off[t] = x;
 }
 
-// Offset scan of the tile totals, in place (one CTA; the tile count is small).
+// Exclusive scan of the tile totals in tile_off (in place) by one CTA of
+// 1024 threads, in chunks of kScanPer x 1024 tiles: each chunk is staged in
+// shared memory with coalesced loads (padded one word per kScanPer so that
+// each thread's run of kScanPer consecutive values is read without bank
+// conflicts), scanned as per-thread runs plus a block scan of the run sums,
+// and written back coalesced; a carry links the chunks.
+constexpr int kScanPer = 8;
+constexpr int kScanTile = 1024 * kScanPer;
+
+__device__ __forceinline__ int scan_slot(int q) { return q + q / kScanPer; }
+
 __global__ void __launch_bounds__(1024) k_scan_tiles(int n_tiles, Workspace W)
 {
+    __shared__ unsigned sv[kScanTile + kScanTile / kScanPer];
     __shared__ unsigned warp_tot[32];
-    const int T = n_tiles;
-    const int per = (T + blockDim.x - 1) / blockDim.x;
-    const int beg = min(T, (int)threadIdx.x * per);
-    const int end = min(T, beg + per);
-    unsigned sum = 0;
-    for (int q = beg; q < end; ++q) sum += W.tile_off[q];
-    // inclusive warp scan
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned v = sum;
+    const int T = n_tiles, tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    unsigned carry = 0;
+    for (int c0 = 0; c0 < T; c0 += kScanTile) {
+        const int n = min(kScanTile, T - c0);
+        for (int q = tid; q < kScanTile; q += 1024) sv[scan_slot(q)] = q < n ? W.tile_off[c0 + q] : 0u;
+        __syncthreads();
+        unsigned run[kScanPer], sum = 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned y = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += y;
-    }
-    if (lane == 31) warp_tot[warp] = v;
-    __syncthreads();
-    if (warp == 0) {
-        unsigned w = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0u;
+        for (int i = 0; i < kScanPer; ++i) {
+            run[i] = sv[scan_slot(tid * kScanPer + i)];
+            sum += run[i];
+        }
+        unsigned v = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const unsigned y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
+            const unsigned y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
         }
-        warp_tot[lane] = w;  // inclusive over warps
+        if (lane == 31) warp_tot[warp] = v;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned w = warp_tot[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            warp_tot[lane] = w;  // inclusive over warps
+        }
+        __syncthreads();
+        unsigned off = carry + v - sum + (warp > 0 ? warp_tot[warp - 1] : 0u);
+#pragma unroll
+        for (int i = 0; i < kScanPer; ++i) {
+            sv[scan_slot(tid * kScanPer + i)] = off;
+            off += run[i];
+        }
+        carry += warp_tot[31];
+        __syncthreads();
+        for (int q = tid; q < n; q += 1024) W.tile_off[c0 + q] = sv[scan_slot(q)];
+        __syncthreads();
     }
-    __syncthreads();
-    unsigned run = v - sum + (warp > 0 ? warp_tot[warp - 1] : 0u);
-    for (int q = beg; q < end; ++q) {
-        const unsigned c = W.tile_off[q];
-        W.tile_off[q] = run;
-        run += c;
-    }
-    if (threadIdx.x == 0) {
-        const unsigned total = warp_tot[(blockDim.x >> 5) - 1];
-        W.tile_off[T] = total;
-        if (total > W.capacity) raise_flag(W.status, TP_FLAG_CAPACITY);
+    if (tid == 0) {
+        W.tile_off[T] = carry;
+        if (carry > W.capacity) raise_flag(W.status, TP_FLAG_CAPACITY);
     }
 }
 
