@@ -108,7 +108,7 @@ typedef enum {
     TP_ERR_INVALID_ARG = 1, /* null pointer, bad size or config (host check) */
     TP_ERR_CAPACITY = 2,    /* workspace too small for the frame's tile lists */
     TP_ERR_NONFINITE = 3,   /* a point had a non-finite input or s_w < 0; it was culled */
-    TP_ERR_TIMEOUT = 4,     /* a bounded device wait gave up */
+    TP_ERR_TIMEOUT = 4,     /* a bounded device wait gave up (no current kernel waits on the device) */
     TP_ERR_CUDA = 5,        /* a CUDA runtime call or launch failed */
     TP_ERR_UNSUPPORTED = 6  /* valid but not supported by this build (e.g. K) */
 } tp_status;

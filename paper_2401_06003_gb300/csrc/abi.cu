@@ -443,6 +443,6 @@ const char *tp_status_string(tp_status status)
     return "unknown status";
 }
 
-int32_t tp_version(void) { return 110; }
+int32_t tp_version(void) { return 120; }
 
 }  // extern "C"
