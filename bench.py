@@ -47,6 +47,9 @@ def parse_args():
     ap.add_argument("--points", type=int, default=0, help="override the workload's point count (profiling)")
     ap.add_argument("--desc-dtype", choices=["auto", "f32", "bf16"], default="auto",
                     help="descriptor storage type (auto: bf16 for the *_bf16 workloads)")
+    ap.add_argument("--point-order", choices=["spatial", "generation"], default="spatial",
+                    help="spatial: relabel the cloud once along a Morton curve (tp_spatial_order, untimed) before "
+                         "timing; generation: the order the generator draws (random within each component)")
     ap.add_argument("--ref-sample", type=int, default=2_000_000, help="points per reference-arm step")
     ap.add_argument("--cpu-frames", type=int, default=2, help="full oracle frames timed for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -239,6 +242,44 @@ def algorithmic_bytes(N, V, F, P, D, b):
 # the CUDA path
 # ---------------------------------------------------------------------------
 
+def relabel_cloud(args, step, tensors, stream, dev):
+    """With --point-order spatial: time `step` on the cloud as generated, then
+    relabel every per-point tensor once along the Morton curve of the cloud
+    (tp_spatial_order + tp_permute_rows; outside the timed region) and return
+    the relabeled tensors (the same for the caller, in place of `tensors`)."""
+    import torch
+
+    from paper_2401_06003_gb300 import permute_rows, spatial_order
+
+    if args.point_order != "spatial":
+        return {"kind": "generation", "tensors": tensors}
+    step_ms = None
+    if args.steps > 0:
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize(dev)
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(args.steps):
+            step()
+        g1.record(stream)
+        torch.cuda.synchronize(dev)
+        step_ms = g0.elapsed_time(g1) / args.steps
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    perm = spatial_order(tensors[0])
+    out = [permute_rows(t, perm) for t in tensors]
+    r1.record(stream)
+    torch.cuda.synchronize(dev)
+    for dst, src in zip(tensors, out):  # the step closure reads the original tensors: overwrite them
+        dst.copy_(src)
+    torch.cuda.synchronize(dev)
+    return {"kind": "spatial (Morton order, tp_spatial_order, once per cloud, untimed)",
+            "relabel_ms": round(r0.elapsed_time(r1), 3),
+            "generation_order_ms_per_step": None if step_ms is None else round(step_ms, 4),
+            "tensors": tensors}
+
+
 def run_ours(args):
     import torch
 
@@ -289,6 +330,9 @@ def run_ours(args):
         r.splat_backward(rec, op, desc, G, ws, kept if store else None, nk if store else None, grads=grads)
         if ev is not None:
             ev[4].record(stream)
+
+    order = relabel_cloud(args, step, [pos, sw, op, desc], stream, dev)
+    pos, sw, op, desc = order.pop("tensors")
 
     for _ in range(args.warmup):
         step()
@@ -350,8 +394,8 @@ def run_ours(args):
     # overlap step k's kernels (the renderer's calls take any stream).
     e2e = None
     if not args.no_e2e:
-        h_in = [torch.from_numpy(sc.pos).pin_memory(), torch.from_numpy(sc.size_w).pin_memory(),
-                torch.from_numpy(sc.opacity).pin_memory(), torch.from_numpy(sc.desc).to(desc_dtype).pin_memory()]
+        # the host copy of the cloud is stored in the same (relabeled) order
+        h_in = [t.cpu().pin_memory() for t in (pos, sw, op, desc)]
         d_in = [[pos, sw, op, desc], [torch.empty_like(t) for t in (pos, sw, op, desc)]]
         d_gr = [list(grads), [torch.empty_like(g) for g in grads]]
         h_out = [[torch.empty(g.shape, dtype=torch.float32).pin_memory() for g in grads] for _ in range(2)]
@@ -496,12 +540,14 @@ def run_ours(args):
                        "height": sc.camera.height, "layers": sc.n_layers, "K": sc.K, "D": D,
                        "desc_dtype": "bf16" if b == 2 else "f32",
                        "mode": args.mode, "tile": args.tile, "parallelism": f"replicas{world}",
+                       "point_order": order["kind"],
                        "l2": f"inputs larger than L2 ({(20 + b * D) * N / 1e6:.0f} MB of point inputs per step); "
                              "no flush"},
             "forward_ms": round(fwd_ms, 4), "fwd_bwd_ms": round(ms_per_step, 4),
             "forward_mpoints_s": round(N / (fwd_ms * 1e-3) / 1e6, 3),
             "counters": {"N": N, "V": V, "F": F, "Fk": Fk, "P": P},
-            "roofline": roofline, "camera_backward": camera, "pyramid_merge": merge, "point_size_init": size_init,
+            "roofline": roofline, "point_order": order, "camera_backward": camera, "pyramid_merge": merge,
+            "point_size_init": size_init,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": KERNELS_PER_STEP * args.steps, "clocks": clk, "device_flags": flags,
@@ -528,6 +574,11 @@ def run_batch(args):
     sw = torch.from_numpy(sc.size_w).to(dev)
     op = torch.from_numpy(sc.opacity).to(dev)
     desc = torch.from_numpy(sc.desc).to(dev)
+    if args.point_order == "spatial":
+        from paper_2401_06003_gb300 import permute_rows, spatial_order
+
+        perm = spatial_order(pos)
+        pos, sw, op, desc = (permute_rows(t, perm) for t in (pos, sw, op, desc))
     t0 = time.perf_counter()
     tiles, tuning = autotune_batch_tiles(sc.cameras, sc.n_layers, pos, sw, op, desc, K=sc.K, device=dev)
     tune_s = time.perf_counter() - t0
@@ -619,6 +670,7 @@ def run_batch(args):
             "config": {"workload": args.workload, "points": N, "views": V,
                        "resolutions": [[c.width, c.height] for c in sc.cameras], "layers": sc.n_layers,
                        "K": sc.K, "D": D, "mode": "recompute", "graph": "one CUDA graph per fwd+bwd batch step",
+                       "point_order": args.point_order,
                        "l2": "inputs larger than L2; no flush"},
             "batch_step_ms": {"p50": round(float(np.percentile(step_ms, 50)), 4),
                               "p99": round(float(np.percentile(step_ms, 99)), 4)},

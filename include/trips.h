@@ -290,6 +290,40 @@ TP_API int64_t tp_init_sizes_workspace_bytes(int64_t n_points);
 TP_API tp_status tp_init_point_sizes(int64_t n, const float *pos, float *size_w, void *ws, int64_t ws_bytes,
                                      tp_stream_t stream);
 
+/*
+ * Spatial order of a point cloud (a one-time relabeling of the points; not a
+ * step of the render path, and the paper has no counterpart).  The render
+ * kernels touch a point's data at every stage -- its tile counters and
+ * tile-list appends, its descriptor row, its gradient rows -- and the points
+ * that meet in one screen tile are neighbours in space; stored along a
+ * space-filling curve they share cache lines and DRAM pages.  A caller that
+ * owns the cloud's storage can relabel it once (and again after large
+ * position updates); every result is the same up to the relabeling, except
+ * that fragments at exactly equal depth are ordered by the new indices.
+ *
+ * tp_spatial_order: perm [n] (device, uint32, written) lists the point
+ *   indices sorted stably by the Morton code of each point's cell in a
+ *   1024^3 grid over the bounding box of the finite points: with
+ *   lo = the box minimum, e = its largest side and s = 1023 / e (float32),
+ *   the cell coordinate along each axis is q = clamp((int)((p - lo) * s),
+ *   0, 1023) in float32 (0 for a box of one position), and the code
+ *   interleaves the bits of qx, qy, qz, x in the lowest bit of each triple.
+ *   Points with a non-finite coordinate come last.  pos [n][3] (device).
+ *   ws: device workspace of tp_spatial_order_workspace_bytes(n) bytes,
+ *   256-byte aligned (about 16 n bytes).  n < 2^31.
+ * tp_permute_rows: dst row k = src row perm[k] for k < n, rows of row_bytes
+ *   bytes (a multiple of 4); src, dst (device, 4-byte aligned, distinct),
+ *   perm [n] (device).  Apply it to every per-point array (positions, sizes,
+ *   opacities, descriptors) with the same perm.
+ */
+TP_API int64_t tp_spatial_order_workspace_bytes(int64_t n_points);
+
+TP_API tp_status tp_spatial_order(int64_t n, const float *pos, uint32_t *perm, void *ws, int64_t ws_bytes,
+                                  tp_stream_t stream);
+
+TP_API tp_status tp_permute_rows(int64_t n, int32_t row_bytes, const void *src, const uint32_t *perm, void *dst,
+                                 tp_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * Batches of views.  Up to TP_MAX_VIEWS cameras (each with its own
  * resolution and screen tile) are rendered from one point cloud by the same

@@ -73,6 +73,9 @@ _SIGS = {
     "tp_merge_backward": (ctypes.c_int, [ctypes.POINTER(tp_camera), ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
     "tp_render_forward_static": (ctypes.c_int, [ctypes.POINTER(tp_config), ctypes.POINTER(tp_camera), _I64, _P, _P,
                                                 _P, _P, _P, _P, _P, _P]),
+    "tp_spatial_order_workspace_bytes": (_I64, [_I64]),
+    "tp_spatial_order": (ctypes.c_int, [_I64, _P, _P, _P, _I64, _P]),
+    "tp_permute_rows": (ctypes.c_int, [_I64, ctypes.c_int32, _P, _P, _P, _P]),
     "tp_get_status": (ctypes.c_int, [_P, _P, ctypes.POINTER(ctypes.c_int32)]),
     "tp_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "tp_version": (ctypes.c_int32, []),

@@ -525,3 +525,42 @@ def init_point_sizes(pos: torch.Tensor, out: torch.Tensor | None = None, ws: tor
     st = lib.tp_init_point_sizes(n, _ptr(pos), _ptr(out), _ptr(ws), ws.numel(), _stream(dev))
     _lib.check("tp_init_point_sizes", st)
     return out
+
+
+def spatial_order(pos: torch.Tensor, ws: torch.Tensor | None = None) -> torch.Tensor:
+    """Point indices [n] (int32 view of uint32) sorted by the Morton code of each
+    point's cell in a 1024^3 grid over the cloud's bounding box (on the GPU).
+
+    Relabel a cloud once with ``permute_rows`` (every per-point array with the
+    same order) so that the points that meet in a screen tile are neighbours in
+    memory; renders are the same up to the relabeling.
+    """
+    lib = _lib.load()
+    if pos.dtype != torch.float32 or pos.dim() != 2 or pos.shape[1] != 3 or not pos.is_contiguous():
+        raise ValueError("pos: expected contiguous float32 [n, 3]")
+    n = pos.shape[0]
+    dev = pos.device
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    need = int(lib.tp_spatial_order_workspace_bytes(n))
+    if need < 0:
+        raise ValueError("too many points")
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+    st = lib.tp_spatial_order(n, _ptr(pos), _ptr(perm), _ptr(ws), ws.numel(), _stream(dev))
+    _lib.check("tp_spatial_order", st)
+    return perm
+
+
+def permute_rows(t: torch.Tensor, perm: torch.Tensor) -> torch.Tensor:
+    """A new tensor whose row k is row perm[k] of t (rows along dim 0; on the GPU)."""
+    lib = _lib.load()
+    if not t.is_contiguous() or t.dim() < 1:
+        raise ValueError("t: expected a contiguous tensor")
+    if perm.dtype != torch.int32 or perm.shape != (t.shape[0],) or not perm.is_contiguous():
+        raise ValueError("perm: expected contiguous int32 [n]")
+    out = torch.empty_like(t)
+    n = t.shape[0]
+    row_bytes = t.numel() // max(n, 1) * t.element_size() if n else 4
+    st = lib.tp_permute_rows(n, row_bytes, _ptr(t), _ptr(perm), _ptr(out), _stream(t.device))
+    _lib.check("tp_permute_rows", st)
+    return out
