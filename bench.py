@@ -15,8 +15,6 @@ per step).
 from __future__ import annotations
 
 import argparse
-import hashlib
-import glob
 import json
 import os
 import subprocess
@@ -50,7 +48,6 @@ def parse_args():
     ap.add_argument("--point-order", choices=["spatial", "generation"], default="spatial",
                     help="spatial: relabel the cloud once along a Morton curve (tp_spatial_order, untimed) before "
                          "timing; generation: the order the generator draws (random within each component)")
-    ap.add_argument("--ref-sample", type=int, default=2_000_000, help="points per reference-arm step")
     ap.add_argument("--cpu-frames", type=int, default=2, help="full oracle frames timed for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -172,34 +169,31 @@ def measured_hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def _code_hash(texts):
-    import re
-
-    h = hashlib.sha256()
-    for name, text in texts:
-        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
-        text = re.sub(r"//[^\n]*", " ", text)
-        h.update(name.encode())
-        h.update(" ".join(text.split()).encode())
-    return h.hexdigest()[:16]
-
-
 # the source files each profiled kernel is compiled from
 KERNEL_FILES = {"k_project_count": ("bin.cu", "common.cuh"), "k_fill": ("bin.cu", "common.cuh"),
                 "k_tile_blend": ("blend.cu", "common.cuh"), "k_tile_backward": ("blend.cu", "common.cuh")}
 
 
 def source_hash(files=None):
-    """Hash of the kernel sources' code (all of csrc/, or the named files),
-    comments and whitespace removed, so an edited comment does not disown the
-    recorded ncu counters."""
-    csrc = os.path.join(ROOT, "paper_2401_06003_gb300", "csrc")
-    paths = sorted(glob.glob(os.path.join(csrc, "*"))) if files is None else [os.path.join(csrc, f) for f in files]
-    texts = []
-    for p in paths:
-        with open(p, encoding="utf-8") as fh:
-            texts.append((os.path.basename(p), fh.read()))
-    return _code_hash(texts)
+    """Hash of the kernel sources' code (comments and whitespace removed)."""
+    from paper_2401_06003_gb300.build import source_hash as _hash
+
+    return _hash(files)
+
+
+def accuracy_report(workload):
+    """The committed accuracy report of `workload` (pyramid and gradient errors
+    against the float64 oracle, written by the GPU parity test), if it was
+    taken from the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", f"accuracy_{workload}.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if d.get("source_hash") != source_hash():
+        return None
+    return d
 
 
 def ncu_traffic(kernel, workload, points):
@@ -461,6 +455,32 @@ def run_ours(args):
     fwd_ms = max_over_ranks(f0.elapsed_time(f1), world, dev) / args.steps
     flags = r.status(ws)
 
+    # the plain float32 form of a bfloat16 workload: the same step with float32 descriptors
+    f32_form = None
+    if b == 2 and not args.no_extras:
+        rf = Renderer(sc.camera, sc.n_layers, K=sc.K, D=sc.D, desc_dtype=torch.float32, mode=args.mode,
+                      tile=(tw, th), device=dev)
+        desc32 = desc.to(torch.float32).contiguous()
+
+        def step32():
+            rf.project(pos, sw, ws, records=rec)
+            rf.splat_forward(rec, op, ws)
+            _, k32, n32, _, _ = rf.blend(N, desc32, ws, store_lists=store, pyramid=pyr)
+            rf.splat_backward(rec, op, desc32, G, ws, k32 if store else None, n32 if store else None, grads=grads)
+
+        for _ in range(args.warmup):
+            step32()
+        torch.cuda.synchronize(dev)
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        for _ in range(args.steps):
+            step32()
+        q1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms32 = max_over_ranks(q0.elapsed_time(q1), world, dev) / args.steps
+        f32_form = {"ms_per_step": round(ms32, 4), "bf16_speedup": round(ms32 / ms_per_step, 3)}
+        del desc32
+
     camera = merge = size_init = None
     if not args.no_extras:
         # camera adjoint of the same frame (one pass over the points' gradients;
@@ -528,7 +548,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(sc, args.cpu_frames)
+        cpu = cpu_baseline(sc, args.cpu_frames, args.workload, N)
 
     if rank == 0:
         line = {
@@ -548,6 +568,7 @@ def run_ours(args):
             "counters": {"N": N, "V": V, "F": F, "Fk": Fk, "P": P},
             "roofline": roofline, "point_order": order, "camera_backward": camera, "pyramid_merge": merge,
             "point_size_init": size_init,
+            "f32_form": f32_form, "accuracy": accuracy_report(args.workload) if b == 2 else None,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": KERNELS_PER_STEP * args.steps, "clocks": clk, "device_flags": flags,
@@ -699,17 +720,95 @@ def _oracle_frame_fwd_bwd(sc, G_seed=1):
     fr.backward(G)
 
 
-def cpu_baseline(sc, frames):
+def _band_worker(workload, n, band, n_bands, G_seed, cmd_q, res_q):
+    """One process of the multi-core oracle: the frame's pyramid rows
+    [band P / n_bands, (band + 1) P / n_bands), rendered and back-propagated
+    by the oracle as it stands, once per command.  The per-band gradients sum
+    to the frame's (the loss is a sum over pixels)."""
+    import oracle
+    from paper_2401_06003_gb300 import scenes
+
+    oracle.build()
+    sc = scenes.make_config(workload, n=n)
+    cam = sc.camera
+    P = int(oracle.pyramid_layout(cam.width, cam.height, sc.n_layers)[0][-1])
+    edges = np.linspace(0, P, n_bands + 1).astype(np.int64)
+    pix = np.arange(edges[band], edges[band + 1], dtype=np.int64)
+    G = np.random.default_rng(G_seed).uniform(-1, 1, (P, sc.D))[pix]
+    res_q.put(("ready", band))
+    while cmd_q.get() is not None:
+        t = time.perf_counter()
+        fr = oracle.Frame.from_scene(sc, pixels=pix)
+        fr.render()
+        fr.backward(G)
+        del fr
+        res_q.put(("done", time.perf_counter() - t))
+
+
+class OraclePool:
+    """The float64 oracle on every host core: one process per core, each on its
+    own band of pyramid rows of the full frame.  Started with the spawn method
+    (the parent may hold a CUDA context)."""
+
+    def __init__(self, workload, n, workers):
+        import multiprocessing as mp
+
+        ctx = mp.get_context("spawn")
+        self.res_q = ctx.Queue()
+        self.cmd_qs = [ctx.Queue() for _ in range(workers)]
+        self.procs = [ctx.Process(target=_band_worker, args=(workload, n, b, workers, 1, self.cmd_qs[b], self.res_q),
+                                  daemon=True) for b in range(workers)]
+        for p in self.procs:
+            p.start()
+        for _ in range(workers):
+            kind, _ = self.res_q.get(timeout=600)
+            assert kind == "ready"
+        self.workers = workers
+
+    def frame(self):
+        """Wall seconds of one full frame (render + backward) over all workers."""
+        t = time.perf_counter()
+        for q in self.cmd_qs:
+            q.put(1)
+        for _ in range(self.workers):
+            kind, _ = self.res_q.get(timeout=600)
+            assert kind == "done"
+        return time.perf_counter() - t
+
+    def close(self):
+        for q in self.cmd_qs:
+            q.put(None)
+        for p in self.procs:
+            p.join(timeout=60)
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(sc, frames, workload, n):
+    """The float64 oracle, as it stands, on the full frame: once on one core
+    and `frames` times on every host core (one process per core)."""
     import oracle
 
     oracle.build()
     t = time.perf_counter()
-    for _ in range(frames):
-        _oracle_frame_fwd_bwd(sc)
-    dt = (time.perf_counter() - t) / frames
-    return {"value": round(sc.n / dt / 1e6, 4), "unit": "Mpoints/s", "cores": 1, "kind": "oracle",
-            "sample": f"{frames} full frames of {sc.name}: fwd+bwd, float64 oracle, 1 thread",
-            "seconds_per_frame": round(dt, 3)}
+    _oracle_frame_fwd_bwd(sc)
+    single = time.perf_counter() - t
+    cores = host_cores()
+    pool = OraclePool(workload, n, cores)
+    try:
+        dt = float(np.median([pool.frame() for _ in range(frames)]))
+    finally:
+        pool.close()
+    return {"value": round(sc.n / dt / 1e6, 4), "unit": "Mpoints/s", "cores": cores, "kind": "oracle",
+            "sample": f"{frames} full frames of {sc.name} (fwd+bwd, float64 oracle), each split into {cores} bands "
+                      f"of pyramid rows, one process per host core",
+            "seconds_per_frame": round(dt, 3),
+            "single_core": {"value": round(sc.n / single / 1e6, 4), "seconds_per_frame": round(single, 3)}}
 
 
 def run_reference(args):
@@ -720,28 +819,27 @@ def run_reference(args):
     from paper_2401_06003_gb300 import scenes
 
     oracle.build()
-    sc = scenes.make_config(args.workload)
-    rng = np.random.default_rng(7)
-    n_s = min(args.ref_sample, sc.n)
-    subs = [sc.subset(np.sort(rng.choice(sc.n, n_s, replace=False))) for _ in range(2)]
-    for w in range(args.warmup):
-        _oracle_frame_fwd_bwd(subs[w % 2])
-    times = []
-    for s in range(args.steps):
-        t = time.perf_counter()
-        _oracle_frame_fwd_bwd(subs[s % 2])
-        times.append(time.perf_counter() - t)
+    sc = scenes.make_config(args.workload, n=args.points or None)
+    cores = host_cores()
+    pool = OraclePool(args.workload, sc.n, cores)
+    try:
+        for _ in range(args.warmup):
+            pool.frame()
+        times = [pool.frame() for _ in range(args.steps)]
+    finally:
+        pool.close()
     ms = 1e3 * float(np.mean(times))
-    value = n_s / (ms * 1e-3) / 1e6
-    sample = f"random {n_s}-point subset of {sc.name} per step (fwd+bwd, float64 oracle, 1 thread)"
+    value = sc.n / (ms * 1e-3) / 1e6
+    sample = (f"full frames of {sc.name} (fwd+bwd, float64 oracle), each split into {cores} bands of pyramid rows, "
+              f"one process per host core")
     line = {
         "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "Mpoints/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "points": sc.n, "width": sc.camera.width,
                    "height": sc.camera.height, "layers": sc.n_layers, "K": sc.K, "D": sc.D,
-                   "mode": "full lists (oracle)", "parallelism": "cpu"},
-        "cpu_baseline": {"value": round(value, 4), "unit": "Mpoints/s", "cores": 1, "kind": "oracle",
+                   "mode": "full lists (oracle)", "parallelism": f"cpu{cores}"},
+        "cpu_baseline": {"value": round(value, 4), "unit": "Mpoints/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(value, 4), "unit": "Mpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }

@@ -80,7 +80,8 @@
  *   transmittance left after the kept fragments; n_frag [P] uint32 is the
  *   number of candidate fragments of the pixel before the K cap.
  *
- * Sizes: n < 2^27 points, 1 <= n_layers <= 16, K in {4, 8, 16, 32},
+ * Sizes: n < 2^27 points (and n x views < 2^29 for batches of views: the
+ * tile offsets are 32-bit), 1 <= n_layers <= 16, K in {4, 8, 16, 32},
  * 1 <= D <= 64, width and height in [1, 32768], tile_w * tile_h <= 1024 (a
  * tile whose CTA does not fit the kernel's registers returns TP_ERR_UNSUPPORTED).
  */
@@ -178,7 +179,8 @@ TP_API tp_status tp_project(const tp_config *cfg, const tp_camera *cam, int64_t 
  * same frame first.
  *   records [n][4] (device, read; from tp_project), opacity [n] (device, read)
  * If the lists exceed the workspace's entry capacity, TP_FLAG_CAPACITY is set
- * and the frame's outputs are not valid.
+ * and the frame's outputs are not valid; the splatting, blend and backward
+ * kernels of that frame then skip their work.
  */
 TP_API tp_status tp_splat_forward(const tp_config *cfg, const tp_camera *cam, int64_t n, const float *records,
                                   const float *opacity, void *ws, int64_t ws_bytes, tp_stream_t stream);
@@ -390,9 +392,13 @@ TP_API tp_status tp_batch_splat_backward(const tp_config *cfg, const tp_camera *
  *   TP_STATIC_WORKSPACE_BYTES: about 190 bytes per point plus 8 per pyramid
  *   pixel, so some 340 thousand points at 256 x 256 with 4 layers and 200
  *   thousand at 1920 x 1080 with 8 layers.
- * - The first call on a device, with that device current, looks up the
- *   array's device address once; make that first call before any stream
- *   capture begins (for instance once at start-up).
+ * - The first call on a device, with that device current, loads the
+ *   library's module on that device (with CUDA's default lazy loading this
+ *   is when the array is reserved, so that first call can fail for lack of
+ *   device memory, as TP_ERR_CUDA) and looks up the array's device address
+ *   once; make that first call at start-up, before any stream capture
+ *   begins.  A cudaDeviceReset voids the looked-up address: call nothing
+ *   here on a device after resetting it.
  * - Every call on a device uses the same array, and each call starts by
  *   resetting the parts that must begin at zero.  Calls that can run at the
  *   same time on the GPU (unordered streams, several host threads) race on

@@ -40,6 +40,27 @@ def _deps():
     return _sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(INCLUDE, "trips.h")]
 
 
+def source_hash(files=None) -> str:
+    """Hash of the kernel sources' code (all of csrc/, or the named files),
+    comments and whitespace removed: recorded next to measurements (ncu
+    counters, accuracy reports) so that they are used only while the code they
+    were taken from is unchanged."""
+    import hashlib
+    import re
+
+    paths = _sources() + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) if files is None else \
+        [os.path.join(CSRC, f) for f in files]
+    h = hashlib.sha256()
+    for p in sorted(paths):
+        with open(p, encoding="utf-8") as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(os.path.basename(p).encode())
+        h.update(" ".join(text.split()).encode())
+    return h.hexdigest()[:16]
+
+
 def up_to_date() -> bool:
     if not os.path.exists(LIB):
         return False

@@ -201,6 +201,8 @@ tp_status batch_checks(const tp_config *cfg, const tp_camera *cams, const int32_
                        void *ws, int64_t ws_bytes, Batch<MaxV> &B, Workspace &W)
 {
     if (n < 0 || n >= kMaxPoints) return TP_ERR_INVALID_ARG;
+    // a point makes at most 8 (point, tile) entries per view; the tile offsets are 32-bit
+    if (n * (int64_t)(n_views > 0 ? n_views : 1) * 8 >= ((int64_t)1 << 32)) return TP_ERR_INVALID_ARG;
     tp_status s = make_batch(cfg, cams, tiles, n_views, B);
     if (s != TP_OK) return s;
     return bind_workspace(B.n_tiles, B.n_pix, ws, ws_bytes, W);
@@ -307,6 +309,7 @@ int64_t batch_workspace_bytes(const tp_config *cfg, const tp_camera *cams, const
 {
     Batch<MaxV> B;
     if (n_points < 0 || n_points >= kMaxPoints) return -1;
+    if (n_points * (int64_t)(n_views > 0 ? n_views : 1) * 8 >= ((int64_t)1 << 32)) return -1;
     if (make_batch(cfg, cams, tiles, n_views, B) != TP_OK) return -1;
     int64_t cap = entry_capacity > 0 ? entry_capacity : 8 * n_points * n_views;
     if (cap < 1) cap = 1;

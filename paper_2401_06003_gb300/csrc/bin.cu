@@ -157,6 +157,7 @@ __global__ void __launch_bounds__(kBlock) k_fill(const __grid_constant__ Batch<M
     const float4 *__restrict__ rec = rec_all + (long long)v * n;
     const unsigned *__restrict__ tile_off = W.tile_off + B.tile_base[v];
     unsigned *__restrict__ cursor = W.tile_cursor + (size_t)B.tile_base[v] * kCopies;
+    if (*((volatile unsigned *)W.status) & TP_FLAG_CAPACITY) return;  // the lists do not fit: outputs invalid
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const float4 r = rec[i];

@@ -372,6 +372,7 @@ __global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_blend(const __grid_consta
                              unsigned *__restrict__ n_frag)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (*((volatile unsigned *)W.status) & TP_FLAG_CAPACITY) return;  // the lists were cut short: outputs invalid
     const int tile = blockIdx.x;  // global over the batch
     const int v = view_of_tile(B, tile);
     const Frame &F = B.view[v];
@@ -529,6 +530,7 @@ __global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_backward(const __grid_con
                                 float *__restrict__ gop, float *__restrict__ gdesc)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (*((volatile unsigned *)W.status) & TP_FLAG_CAPACITY) return;  // the lists were cut short: outputs invalid
     const int tile = blockIdx.x;  // global over the batch
     const int v = view_of_tile(B, tile);
     const Frame &F = B.view[v];

@@ -8,10 +8,15 @@
 // the frame's workspace is the array below instead of a caller buffer.
 //
 // The array belongs to the library's device image: every GPU that loads the
-// library holds TP_STATIC_WORKSPACE_BYTES of it until the process exits.  In
-// host code its name only stands for the device symbol; the device address is
-// looked up with cudaGetSymbolAddress once per device, by the first call made
-// with that device current.  All calls on a device share the array, so calls
+// library's module holds TP_STATIC_WORKSPACE_BYTES of it until the process
+// exits.  With lazy module loading (the CUDA default) the module, and with it
+// the array, is loaded and reserved by the first call on each device, which
+// can therefore fail for lack of device memory (TP_ERR_CUDA): make that first
+// call at start-up.  In host code the array's name only stands for the
+// device symbol; the device address is looked up with cudaGetSymbolAddress
+// once per device, by the first call made with that device current, and
+// cached; a cudaDeviceReset of that device voids the cached address, and a
+// later call looks it up again only if the lookup itself fails.  All calls on a device share the array, so calls
 // that overlap on the GPU race; ordered calls do not, because each call resets
 // what must start at zero and overwrites everything else it reads.
 #include <mutex>

@@ -80,3 +80,14 @@ def test_size_limits_are_refused_on_the_host(lib):
     assert lib.tp_workspace_bytes(ctypes.byref(cfg), ctypes.byref(wide), 10, 0) > 0
     wide.width = 32769
     assert lib.tp_workspace_bytes(ctypes.byref(cfg), ctypes.byref(wide), 10, 0) == -1
+
+
+def test_batch_entry_offsets_stay_32_bit(lib):
+    """A batch may hold at most 8 (point, tile) entries per point and view below 2^32:
+    n x views < 2^29 (the tile offsets are 32-bit)."""
+    cams = (_lib.tp_camera * 16)(*[_lib.make_camera(scenes.make_config("cube20k_256", n=10).camera)] * 16)
+    cfg = _lib.make_config(4, 16, 4)
+    assert lib.tp_batch_workspace_bytes(ctypes.byref(cfg), cams, None, 16, (1 << 25) - 1, 1) > 0
+    assert lib.tp_batch_workspace_bytes(ctypes.byref(cfg), cams, None, 16, 1 << 25, 1) == -1
+    assert lib.tp_batch_workspace_bytes(ctypes.byref(cfg), cams, None, 8, (1 << 27) - 1, 1) == -1
+    assert lib.tp_batch_workspace_bytes(ctypes.byref(cfg), cams, None, 2, (1 << 27) - 1, 1) > 0

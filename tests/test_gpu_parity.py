@@ -309,6 +309,12 @@ def test_ground10m_4k_bf16_crops():
     o_f32 = _oracle(sc, pixels=pix)
     ref_f = o_f32.render()
     assert_close_scaled(out["pyramid"][rows], ref_f["pyramid"], BF16_RTOL, name="4k bf16 vs oracle(f32)")
+    from paper_2401_06003_gb300.build import source_hash
+
+    report = {"workload": "ground10m_4k_bf16", "source_hash": source_hash(), "crops": "8 seeded 64x64 crops of layer 0 and the coarser pixels "
+              "above them", "pixels": int(rows.size)}
+    report["pyramid"] = {"vs_oracle_bf16_values": _error_stats(out["pyramid"][rows], ref_bf["pyramid"]),
+                         "vs_oracle_f32_values": _error_stats(out["pyramid"][rows], ref_f["pyramid"])}
     err = np.abs(out["pyramid"][rows].astype(np.float64) - ref_f["pyramid"])
     print(f"4K bf16 crops: pyramid max abs err {err.max():.3e}, mean {err.mean():.3e} "
           f"(max |value| {np.abs(ref_f['pyramid']).max():.3f})")
@@ -326,10 +332,30 @@ def test_ground10m_4k_bf16_crops():
     # reported, not asserted; the descriptor and opacity gradients do not
     # depend on tau's rounding except through g_m and stay close.
     ref_gf = o_f32.backward(G[rows].astype(np.float64))
+    report["points_with_gradient"] = int(touched.size)
     for k in ("pos", "size_w", "opacity", "desc"):
+        report[f"grad_{k}"] = {"vs_oracle_bf16_values": _error_stats(got[k][touched], ref_g[k][touched]),
+                               "vs_oracle_f32_values": _error_stats(got[k][touched], ref_gf[k][touched])}
         g_ = got[k][touched].astype(np.float64).ravel()
         o_ = ref_gf[k][touched].ravel()
         e_ = np.abs(g_ - o_)
         print(f"4K bf16 crops: grad_{k} vs oracle(f32 desc): max abs err {e_.max():.3e}, mean {e_.mean():.3e}, "
               f"max |ref| {np.abs(o_).max():.3e}")
+    path = os.environ.get("TRIPS_ACCURACY_REPORT")
+    if path:
+        with open(path, "w") as fh:
+            json.dump(report, fh, indent=1)
     assert_close_scaled(got["desc"][touched], ref_gf["desc"][touched], BF16_RTOL, name="4k bf16 grad_desc vs f32")
+
+
+def _error_stats(got, ref):
+    """Max and mean absolute error, the largest reference magnitude, and the
+    error relative to it (max and mean of |g - o| / (|o| + 1e-3 max|o|))."""
+    g = np.asarray(got, np.float64).ravel()
+    o = np.asarray(ref, np.float64).ravel()
+    e = np.abs(g - o)
+    scale = float(np.abs(o).max()) if o.size else 0.0
+    rel = e / (np.abs(o) + 1e-3 * scale + 1e-300)
+    return {"max_abs": float(e.max()), "mean_abs": float(e.mean()), "max_ref": scale,
+            "max_rel": float(rel.max()), "mean_rel": float(rel.mean()),
+            "frac_rel_above_1e-2": float((rel > 1e-2).mean())}
