@@ -60,7 +60,7 @@ def _load():
         lib.orc_pyramid_layout.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P]
         lib.orc_frame_build.restype = P
         lib.orc_frame_build.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dbl,
-                                        ctypes.c_int, i64, P, P, P, P, ctypes.c_int, i64, P, i64, P]
+                                        ctypes.c_int, i64, P, P, P, P, ctypes.c_int, i64, P, i64, P, ctypes.c_int]
         lib.orc_frame_free.argtypes = [P]
         for name in ("orc_frame_num_pixels", "orc_frame_num_fragments", "orc_frame_num_bad"):
             getattr(lib, name).restype = i64
@@ -99,10 +99,13 @@ class Frame:
     follows from it, in float32 with the operation order the CUDA kernels
     use; ``prec32=False`` is the all-float64 reading (needed for finite
     differences).  Weights, blending and the adjoint are float64 either way.
+    ``coarse=True`` adds the coarse-layer inclusion of Sec. 3.6: a pixel's
+    list also holds the fragments of the coarser-layer pixels that contain it
+    (reading R24 in the C source).
     """
 
     def __init__(self, cam_floats, width, height, n_layers, K, pos, size_w, opacity, desc,
-                 eps=0.25, prec32=True, pixels=None, points=None):
+                 eps=0.25, prec32=True, pixels=None, points=None, coarse=False):
         self._lib = _load()
         self.pos = np.ascontiguousarray(pos, np.float32)
         self.size_w = np.ascontiguousarray(size_w, np.float32)
@@ -121,7 +124,8 @@ class Frame:
         self._h = self._lib.orc_frame_build(
             _ptr(self.cam), self.width, self.height, self.n_layers, self.K, float(eps), self.D,
             self.n, _ptr(self.pos), _ptr(self.size_w), _ptr(self.opacity), _ptr(self.desc),
-            int(self.prec32), 0 if pix is None else pix.size, _ptr(pix), 0 if pts is None else pts.size, _ptr(pts))
+            int(self.prec32), 0 if pix is None else pix.size, _ptr(pix), 0 if pts is None else pts.size, _ptr(pts),
+            int(bool(coarse)))
         if not self._h:
             raise MemoryError("oracle frame build failed")
         self.n_pix = int(self._lib.orc_frame_num_pixels(self._h))
@@ -135,10 +139,11 @@ class Frame:
             self._h = None
 
     @classmethod
-    def from_scene(cls, scene, view=0, prec32=True, pixels=None, points=None, desc=None):
+    def from_scene(cls, scene, view=0, prec32=True, pixels=None, points=None, desc=None, coarse=False):
         cam = scene.cameras[view]
         return cls(cam.as_floats(), cam.width, cam.height, scene.n_layers, scene.K, scene.pos, scene.size_w,
-                   scene.opacity, scene.desc if desc is None else desc, prec32=prec32, pixels=pixels, points=points)
+                   scene.opacity, scene.desc if desc is None else desc, prec32=prec32, pixels=pixels, points=points,
+                   coarse=coarse)
 
     def pixels(self) -> np.ndarray:
         out = np.zeros(self.n_pix, np.int64)

@@ -46,6 +46,12 @@
  *   R11 alpha_m of Eq. 6 is the fragment opacity gamma_m; c_m is the point's
  *       descriptor; no background term; T_final = prod (1 - gamma_m) is
  *       returned as well.
+ *   R24 coarse-layer inclusion (optional, Sec. 3.6 "Implementation
+ *       Details"): the list of pixel (L, j, k) also holds, for every coarser
+ *       layer L' > L, the fragments of the layer-L' pixel that contains it,
+ *       (j >> (L'-L), k >> (L'-L)), each with its own weight gamma (Eq. 3-5 at
+ *       its own layer); lists are ordered by (z, point index, layer), so a
+ *       point's two layers follow each other, the finer first.
  *   R12 precision of the decisions: everything that decides an integer
  *       (culling, layer pair, tap indices, zero weights, depth order) is
  *       taken from the projection evaluated either in IEEE float32 with the
@@ -299,13 +305,15 @@ typedef struct {
     int64_t pix;
     double z;
     int32_t i;
-    int32_t f; /* index into frags */
+    int32_t f;   /* index into frags */
+    int32_t lay; /* the fragment's own layer (R24 tie-break) */
 } okey;
 
 typedef struct {
     ocam cam;
     olayout ly;
     int K, D, prec32;
+    int coarse;        /* R24: lists include the fragments of the containing coarser pixels */
     double eps;
     int64_t n;
     const float *pos, *sw, *alpha, *desc; /* borrowed; must outlive the frame */
@@ -313,9 +321,9 @@ typedef struct {
     int64_t n_pix;
     int64_t *pixels;  /* [n_pix] sorted pyramid pixel ids covered by the frame */
     int full;         /* 1 if pixels == 0..P-1 */
-    int64_t n_frag;
-    ofrag *frags;     /* [n_frag] */
-    okey *keys;       /* [n_frag] sorted by (pix, z, i) */
+    int64_t n_frag;   /* list entries (with coarse inclusion a fragment can be in many lists) */
+    ofrag *frags;     /* the fragments the lists refer to */
+    okey *keys;       /* [n_frag] sorted by (pix, z, i, layer) */
     int64_t *pix_start; /* [n_pix + 1] range of keys of each frame pixel */
     int64_t n_bad;
 } oframe;
@@ -326,6 +334,7 @@ static int cmp_key(const void *pa, const void *pb)
     if (a->pix != b->pix) return a->pix < b->pix ? -1 : 1;
     if (a->z != b->z) return a->z < b->z ? -1 : 1;
     if (a->i != b->i) return a->i < b->i ? -1 : 1;
+    if (a->lay != b->lay) return a->lay < b->lay ? -1 : 1;
     return 0;
 }
 
@@ -363,10 +372,30 @@ void orc_frame_free(oframe *fr)
  * every pixel touched by a point in `pt_sel`; with both empty it covers the
  * whole pyramid.
  */
+/* Calls emit(pix) for the pixel of fragment fr and, with coarse inclusion
+ * (R24), for every pixel of the finer layers that the fragment's pixel
+ * contains. */
+#define FOR_EACH_LIST_PIXEL(ly, fr, coarse, BODY)                                          \
+    do {                                                                                   \
+        const int Lf_ = (fr)->layer;                                                       \
+        const int Lmin_ = (coarse) ? 0 : Lf_;                                              \
+        for (int L_ = Lf_; L_ >= Lmin_; --L_) {                                            \
+            const int d_ = Lf_ - L_;                                                       \
+            const int j0_ = (fr)->j << d_, k0_ = (fr)->k << d_;                           \
+            const int j1_ = ((fr)->j + 1) << d_ < (ly)->w[L_] ? ((fr)->j + 1) << d_ : (ly)->w[L_]; \
+            const int k1_ = ((fr)->k + 1) << d_ < (ly)->h[L_] ? ((fr)->k + 1) << d_ : (ly)->h[L_]; \
+            for (int kk_ = k0_; kk_ < k1_; ++kk_)                                          \
+                for (int jj_ = j0_; jj_ < j1_; ++jj_) {                                    \
+                    const int64_t pix = (ly)->off[L_] + (int64_t)kk_ * (ly)->w[L_] + jj_;  \
+                    BODY;                                                                  \
+                }                                                                          \
+        }                                                                                  \
+    } while (0)
+
 oframe *orc_frame_build(const float *cam17, int W, int H, int n_layers, int K, double eps, int D,
                         int64_t n, const float *pos, const float *sw, const float *alpha, const float *desc,
                         int prec32, int64_t n_pix_sel, const int64_t *pix_sel, int64_t n_pt_sel,
-                        const int64_t *pt_sel)
+                        const int64_t *pt_sel, int coarse)
 {
     if (n_layers < 1 || n_layers > ORC_MAX_LAYERS || K < 1 || D < 1 || n < 0) return NULL;
     oframe *fr = (oframe *)calloc(1, sizeof(oframe));
@@ -375,7 +404,7 @@ oframe *orc_frame_build(const float *cam17, int W, int H, int n_layers, int K, d
     fr->cam.width = W;
     fr->cam.height = H;
     make_layout(W, H, n_layers, &fr->ly);
-    fr->K = K; fr->D = D; fr->eps = eps; fr->prec32 = prec32;
+    fr->K = K; fr->D = D; fr->eps = eps; fr->prec32 = prec32; fr->coarse = coarse != 0;
     fr->n = n; fr->pos = pos; fr->sw = sw; fr->alpha = alpha; fr->desc = desc;
     int64_t P = fr->ly.off[n_layers];
 
@@ -419,33 +448,40 @@ oframe *orc_frame_build(const float *cam17, int W, int H, int n_layers, int K, d
             if (!mask) goto fail;
             for (int64_t q = 0; q < fr->n_pix; ++q) mask[fr->pixels[q]] = 1;
         }
-        int64_t cap = 0;
-        for (int64_t i = 0; i < n; ++i) {
-            ofrag tmp[8];
-            int nf = point_fragments(&fr->proj[i], &fr->ly, prec32, eps, tmp);
-            for (int t = 0; t < nf; ++t)
-                if (!mask || mask[frag_pixel(&fr->ly, &tmp[t])]) ++cap;
-        }
-        fr->frags = (ofrag *)malloc((size_t)(cap > 0 ? cap : 1) * sizeof(ofrag));
-        fr->keys = (okey *)malloc((size_t)(cap > 0 ? cap : 1) * sizeof(okey));
-        if (!fr->frags || !fr->keys) { free(mask); goto fail; }
-        int64_t m = 0;
+        /* every fragment, and one list entry per pixel whose list holds it */
+        int64_t cap_f = 0, cap_k = 0;
         for (int64_t i = 0; i < n; ++i) {
             ofrag tmp[8];
             int nf = point_fragments(&fr->proj[i], &fr->ly, prec32, eps, tmp);
             for (int t = 0; t < nf; ++t) {
-                int64_t pix = frag_pixel(&fr->ly, &tmp[t]);
-                if (mask && !mask[pix]) continue;
-                fr->frags[m] = tmp[t];
-                fr->keys[m].pix = pix;
-                fr->keys[m].z = fr->proj[i].z;
-                fr->keys[m].i = (int32_t)i;
-                fr->keys[m].f = (int32_t)m;
-                ++m;
+                int used = 0;
+                FOR_EACH_LIST_PIXEL(&fr->ly, &tmp[t], fr->coarse, if (!mask || mask[pix]) { ++cap_k; used = 1; });
+                cap_f += used;
+            }
+        }
+        fr->frags = (ofrag *)malloc((size_t)(cap_f > 0 ? cap_f : 1) * sizeof(ofrag));
+        fr->keys = (okey *)malloc((size_t)(cap_k > 0 ? cap_k : 1) * sizeof(okey));
+        if (!fr->frags || !fr->keys) { free(mask); goto fail; }
+        int64_t mf = 0, mk = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            ofrag tmp[8];
+            int nf = point_fragments(&fr->proj[i], &fr->ly, prec32, eps, tmp);
+            for (int t = 0; t < nf; ++t) {
+                int used = 0;
+                FOR_EACH_LIST_PIXEL(&fr->ly, &tmp[t], fr->coarse, if (!mask || mask[pix]) {
+                    fr->keys[mk].pix = pix;
+                    fr->keys[mk].z = fr->proj[i].z;
+                    fr->keys[mk].i = (int32_t)i;
+                    fr->keys[mk].f = (int32_t)mf;
+                    fr->keys[mk].lay = tmp[t].layer;
+                    ++mk;
+                    used = 1;
+                });
+                if (used) fr->frags[mf++] = tmp[t];
             }
         }
         free(mask);
-        fr->n_frag = m;
+        fr->n_frag = mk;
     }
     /* R10: each pixel's list in ascending (z, i). */
     qsort(fr->keys, (size_t)fr->n_frag, sizeof(okey), cmp_key);
@@ -838,11 +874,14 @@ static int same_state(const olocal *a, const olocal *b)
  * identical at -h, 0 and +h (else the entry is 0 and not a derivative).
  * The frame must cover every pixel of the selected points.  In a float32
  * frame the differences are taken around the frame's float32 screen-space
- * state (see eval_proj).  Returns 0, or -1 on bad arguments.
+ * state (see eval_proj).  Returns 0, or -1 on bad arguments (also for a
+ * frame with coarse-layer inclusion, whose lists this local evaluation does
+ * not rebuild).
  */
 int orc_frame_fd(const oframe *fr, const double *G, int64_t n_sel, const int64_t *sel, double h_pos,
                  double h_sw_rel, double h_alpha, double h_desc, double *fd, int8_t *valid)
 {
+    if (fr->coarse) return -1;
     int D = fr->D;
     int np = 5 + D;
     double *d0 = (double *)malloc((size_t)D * sizeof(double));
