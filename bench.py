@@ -481,6 +481,40 @@ def run_ours(args):
         f32_form = {"ms_per_step": round(ms32, 4), "bf16_speedup": round(ms32 / ms_per_step, 3)}
         del desc32
 
+    # the same step with coarse-layer inclusion (Sec. 3.6): lists also hold the
+    # fragments of the coarser pixels above; the blend runs layer by layer
+    inclusion = None
+    if not args.no_extras and not store:
+        rc = Renderer(sc.camera, sc.n_layers, K=sc.K, D=sc.D, desc_dtype=desc_dtype, mode=args.mode,
+                      tile=(tw, th), device=dev, coarse=True)
+        ws_c = rc.new_workspace(N)
+
+        def step_c():
+            rc.project(pos, sw, ws_c, records=rec)
+            rc.splat_forward(rec, op, ws_c)
+            rc.blend(N, desc, ws_c, pyramid=pyr)
+            rc.splat_backward(rec, op, desc, G, ws_c, grads=grads)
+
+        def timed(fn):
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize(dev)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for _ in range(args.steps):
+                fn()
+            a1.record(stream)
+            torch.cuda.synchronize(dev)
+            return max_over_ranks(a0.elapsed_time(a1), world, dev) / args.steps
+
+        ms_c = timed(step_c)
+        fwd_c = timed(lambda: (rc.project(pos, sw, ws_c, records=rec), rc.splat_forward(rec, op, ws_c),
+                               rc.blend(N, desc, ws_c, pyramid=pyr)))
+        inclusion = {"ms_per_step": round(ms_c, 4), "overhead_ms": round(ms_c - ms_per_step, 4),
+                     "forward_ms": round(fwd_c, 4), "forward_overhead_ms": round(fwd_c - fwd_ms, 4),
+                     "flags": rc.status(ws_c), "workspace_bytes": int(ws_c.numel())}
+        del ws_c
+
     camera = merge = size_init = None
     if not args.no_extras:
         # camera adjoint of the same frame (one pass over the points' gradients;
@@ -569,6 +603,7 @@ def run_ours(args):
             "roofline": roofline, "point_order": order, "camera_backward": camera, "pyramid_merge": merge,
             "point_size_init": size_init,
             "f32_form": f32_form, "accuracy": accuracy_report(args.workload) if b == 2 else None,
+            "coarse_inclusion": inclusion,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": KERNELS_PER_STEP * args.steps, "clocks": clk, "device_flags": flags,

@@ -59,7 +59,10 @@
  * - Fragments with an exactly zero bilinear or layer weight are not written;
  *   taps outside a layer are dropped.
  * - Per pixel, fragments are ordered by ascending (z, point index) and the
- *   first K are kept (Sec. 3.2 and Sec. 3.6, K = 16 in the paper).
+ *   first K are kept (Sec. 3.2 and Sec. 3.6, K = 16 in the paper).  With
+ *   coarse-layer inclusion (TP_COARSE_LAYERS) a pixel's list also holds the
+ *   fragments of the coarser pixels that contain it (a point's two layers
+ *   then follow each other, the finer first).
  * - The projection and everything that decides an integer (culling, layer
  *   pair, taps, order) is evaluated in IEEE float32 in this fixed order, with
  *   no fused multiply-add: Xc = ((R0 X + R1 Y) + R2 Z) + t0 (likewise Yc, Zc),
@@ -140,7 +143,23 @@ typedef struct {
     int32_t mode;       /* TP_STORE_LISTS or TP_RECOMPUTE (see tp_splat_backward) */
     int32_t tile_w;     /* screen tile of the binning and blend kernels, in pixels */
     int32_t tile_h;     /*   of each layer; 0 = the default 16 x 8 */
+    int32_t flags;      /* TP_COARSE_LAYERS or 0 */
 } tp_config;
+
+/*
+ * tp_config.flags.  TP_COARSE_LAYERS: coarse-layer inclusion (the paper
+ * includes points from coarser layers during blending, in the usual way, so
+ * that occlusion holds across large differences in point density; Sec. 3.6,
+ * Implementation Details).  The list of pixel (L, j, k) then also holds, for
+ * every coarser layer L' > L, the fragments of the layer-L' pixel that
+ * contains it, (j >> (L'-L), k >> (L'-L)), each with its own weight gamma
+ * (Eq. 3-5 at its own layer), ordered with the pixel's own fragments by
+ * (depth, point index, layer); the first K are blended (Eq. 6-7) and the
+ * gradients flow to every kept instance.  Supported with TP_RECOMPUTE
+ * backward passes (tp_splat_backward returns TP_ERR_UNSUPPORTED for stored
+ * lists, whose point indices do not say which layer's fragment was kept).
+ */
+#define TP_COARSE_LAYERS 0x1
 
 /*
  * Number of pyramid pixels P = sum_L W_L H_L.  If layer_offsets is not NULL

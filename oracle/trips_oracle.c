@@ -420,7 +420,16 @@ oframe *orc_frame_build(const float *cam17, int W, int H, int n_layers, int K, d
         fr->full = 1;
         fr->n_pix = P;
     } else {
-        int64_t cap = (n_pix_sel > 0 ? n_pix_sel : 0) + 8 * (n_pt_sel > 0 ? n_pt_sel : 0);
+        /* a selected point's pixels: every list that holds one of its
+           fragments (with coarse inclusion, also the finer pixels below) */
+        int64_t cap = n_pix_sel > 0 ? n_pix_sel : 0;
+        for (int64_t q = 0; q < n_pt_sel; ++q) {
+            int64_t i = pt_sel[q];
+            if (i < 0 || i >= n) continue;
+            ofrag tmp[8];
+            int nf = point_fragments(&fr->proj[i], &fr->ly, prec32, eps, tmp);
+            for (int t = 0; t < nf; ++t) FOR_EACH_LIST_PIXEL(&fr->ly, &tmp[t], fr->coarse, { (void)pix; ++cap; });
+        }
         fr->pixels = (int64_t *)malloc((size_t)(cap > 0 ? cap : 1) * sizeof(int64_t));
         if (!fr->pixels) goto fail;
         int64_t m = 0;
@@ -431,7 +440,7 @@ oframe *orc_frame_build(const float *cam17, int W, int H, int n_layers, int K, d
             if (i < 0 || i >= n) continue;
             ofrag tmp[8];
             int nf = point_fragments(&fr->proj[i], &fr->ly, prec32, eps, tmp);
-            for (int t = 0; t < nf; ++t) fr->pixels[m++] = frag_pixel(&fr->ly, &tmp[t]);
+            for (int t = 0; t < nf; ++t) FOR_EACH_LIST_PIXEL(&fr->ly, &tmp[t], fr->coarse, { fr->pixels[m++] = pix; });
         }
         qsort(fr->pixels, (size_t)m, sizeof(int64_t), cmp_i64);
         int64_t u = 0;

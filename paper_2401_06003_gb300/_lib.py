@@ -20,6 +20,7 @@ TP_OK, TP_ERR_INVALID_ARG, TP_ERR_CAPACITY, TP_ERR_NONFINITE, TP_ERR_TIMEOUT, TP
 TP_FLAG_NONFINITE, TP_FLAG_CAPACITY, TP_FLAG_TIMEOUT = 0x1, 0x2, 0x4
 TP_F32, TP_BF16 = 0, 1
 TP_STORE_LISTS, TP_RECOMPUTE = 0, 1
+TP_COARSE_LAYERS = 0x1
 
 
 class tp_camera(ctypes.Structure):
@@ -31,7 +32,7 @@ class tp_camera(ctypes.Structure):
 class tp_config(ctypes.Structure):
     _fields_ = [("n_layers", ctypes.c_int32), ("K", ctypes.c_int32), ("desc_dim", ctypes.c_int32),
                 ("eps", ctypes.c_float), ("desc_dtype", ctypes.c_int32), ("mode", ctypes.c_int32),
-                ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32)]
+                ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
 class TripsError(RuntimeError):
@@ -129,5 +130,6 @@ def make_camera(cam) -> tp_camera:
 
 
 def make_config(n_layers: int, K: int, D: int, eps: float = 0.25, desc_dtype: int = TP_F32,
-                mode: int = TP_RECOMPUTE, tile_w: int = 0, tile_h: int = 0) -> tp_config:
-    return tp_config(int(n_layers), int(K), int(D), float(eps), int(desc_dtype), int(mode), int(tile_w), int(tile_h))
+                mode: int = TP_RECOMPUTE, tile_w: int = 0, tile_h: int = 0, flags: int = 0) -> tp_config:
+    return tp_config(int(n_layers), int(K), int(D), float(eps), int(desc_dtype), int(mode), int(tile_w), int(tile_h),
+                     int(flags))

@@ -57,6 +57,7 @@ tp_status check_config(const tp_config *cfg)
     if (cfg->K < 1 || cfg->K > 255) return TP_ERR_INVALID_ARG;
     if (cfg->K != 4 && cfg->K != 8 && cfg->K != 16 && cfg->K != 32) return TP_ERR_UNSUPPORTED;
     if (cfg->tile_w < 0 || cfg->tile_h < 0) return TP_ERR_INVALID_ARG;
+    if ((cfg->flags & ~TP_COARSE_LAYERS) != 0) return TP_ERR_INVALID_ARG;
     return TP_OK;
 }
 
@@ -82,6 +83,7 @@ tp_status make_frame(const tp_config *cfg, const tp_camera *cam, int tw, int th,
     F.D = cfg->desc_dim;
     F.tile_w = tw;
     F.tile_h = th;
+    F.coarse = (cfg->flags & TP_COARSE_LAYERS) ? 1 : 0;
     fill_layers(cam, cfg->n_layers, F);
     int tiles = 0;
     for (int L = 0; L < F.n_layers; ++L) {
@@ -128,6 +130,7 @@ tp_status make_batch(const tp_config *cfg, const tp_camera *cams, const int32_t 
         const Frame &F = B.view[v];
         B.tile_base[v + 1] = B.tile_base[v] + F.n_tiles;
         B.pix_base[v + 1] = B.pix_base[v] + F.pix_base[F.n_layers];
+        B.cpix_base[v + 1] = B.cpix_base[v] + (F.pix_base[F.n_layers] - F.pix_base[1]);
         if (F.tile_threads > B.max_threads) B.max_threads = F.tile_threads;
         if ((int64_t)B.tile_base[v + 1] > ((int64_t)1 << 28)) return TP_ERR_INVALID_ARG;
     }
@@ -143,53 +146,70 @@ tp_status make_batch(const tp_config *cfg, const tp_camera *cams, const int32_t 
 }
 
 // Workspace: status word, tile counts [T][copies], tile offsets [T + 1],
-// fill cursors [T][copies], the per-pixel largest kept keys [P], then the tile
-// lists as two arrays: 8-byte fragment keys and 16-byte payloads.
+// fill cursors [T][copies], the per-pixel largest kept keys [P], with
+// coarse-layer inclusion the kept lists of the coarse pixels ([K][rows] keys,
+// then [K][rows] opacities), then the tile lists as two arrays: 8-byte
+// fragment keys and 16-byte payloads.
 constexpr int64_t kEntryBytes = 24;
 
 struct WsLayout {
-    int64_t count, off, cursor, kmax, key, pay, end;
+    int64_t count, off, cursor, kmax, ckey, cgam, key, pay, end;
 };
 
-WsLayout layout_for(int64_t n_tiles, int64_t n_pix, int64_t capacity)
+// cslots: K x coarse pixels with coarse-layer inclusion, else 0.
+WsLayout layout_for(int64_t n_tiles, int64_t n_pix, int64_t cslots, int64_t capacity)
 {
     WsLayout w;
     w.count = kAlign;
     w.off = align_up(w.count + 4 * n_tiles * tpk::kCopies);
     w.cursor = align_up(w.off + 4 * (n_tiles + 1));
     w.kmax = align_up(w.cursor + 4 * n_tiles * tpk::kCopies);
-    w.key = align_up(w.kmax + 8 * n_pix);
+    w.ckey = align_up(w.kmax + 8 * n_pix);
+    w.cgam = align_up(w.ckey + 8 * cslots);
+    w.key = align_up(w.cgam + 4 * cslots);
     w.pay = align_up(w.key + 8 * capacity);
     w.end = w.pay + 16 * capacity;
     return w;
 }
 
 // Entry capacity that fits in ws_bytes (largest c with layout_for(c).end <= ws_bytes).
-int64_t capacity_for(int64_t n_tiles, int64_t n_pix, int64_t ws_bytes)
+int64_t capacity_for(int64_t n_tiles, int64_t n_pix, int64_t cslots, int64_t ws_bytes)
 {
-    const WsLayout w0 = layout_for(n_tiles, n_pix, 0);
+    const WsLayout w0 = layout_for(n_tiles, n_pix, cslots, 0);
     if (ws_bytes < w0.end) return -1;
     // align_up only adds bytes, so (ws_bytes - key) / 24 is an upper bound;
     // alignment costs < 256 bytes, so the loop runs at most ~11 times.
     int64_t c = (ws_bytes - w0.key) / kEntryBytes;
     if (c < 0) c = 0;
-    while (c > 0 && layout_for(n_tiles, n_pix, c).end > ws_bytes) --c;
+    while (c > 0 && layout_for(n_tiles, n_pix, cslots, c).end > ws_bytes) --c;
     if (c > 0x7FFFFFFF) c = 0x7FFFFFFF;
     return c;
 }
 
-tp_status bind_workspace(int64_t n_tiles, int64_t n_pix, void *ws, int64_t ws_bytes, Workspace &W)
+// K x coarse pixels of the batch with coarse-layer inclusion, else 0.
+template <int MaxV>
+int64_t coarse_slots(const tp_config *cfg, const Batch<MaxV> &B)
+{
+    return (cfg->flags & TP_COARSE_LAYERS) ? (int64_t)cfg->K * B.cpix_base[B.n_views] : 0;
+}
+
+template <int MaxV>
+tp_status bind_workspace(const tp_config *cfg, const Batch<MaxV> &B, void *ws, int64_t ws_bytes, Workspace &W)
 {
     if (!ws || ((uintptr_t)ws % kAlign) != 0) return TP_ERR_INVALID_ARG;
-    const int64_t cap = capacity_for(n_tiles, n_pix, ws_bytes);
+    const int64_t cslots = coarse_slots(cfg, B);
+    const int64_t cap = capacity_for(B.n_tiles, B.n_pix, cslots, ws_bytes);
     if (cap < 1) return TP_ERR_INVALID_ARG;
-    const WsLayout w = layout_for(n_tiles, n_pix, cap);
+    const WsLayout w = layout_for(B.n_tiles, B.n_pix, cslots, cap);
     char *base = static_cast<char *>(ws);
     W.status = reinterpret_cast<unsigned *>(base);
     W.tile_count = reinterpret_cast<unsigned *>(base + w.count);
     W.tile_off = reinterpret_cast<unsigned *>(base + w.off);
     W.tile_cursor = reinterpret_cast<unsigned *>(base + w.cursor);
     W.kmax = reinterpret_cast<unsigned long long *>(base + w.kmax);
+    W.ckey = cslots ? reinterpret_cast<unsigned long long *>(base + w.ckey) : nullptr;
+    W.cgam = cslots ? reinterpret_cast<unsigned *>(base + w.cgam) : nullptr;
+    W.crows = B.cpix_base[B.n_views];
     W.bucket_key = reinterpret_cast<unsigned long long *>(base + w.key);
     W.bucket_pay = reinterpret_cast<float4 *>(base + w.pay);
     W.capacity = (unsigned)cap;
@@ -205,7 +225,7 @@ tp_status batch_checks(const tp_config *cfg, const tp_camera *cams, const int32_
     if (n * (int64_t)(n_views > 0 ? n_views : 1) * 8 >= ((int64_t)1 << 32)) return TP_ERR_INVALID_ARG;
     tp_status s = make_batch(cfg, cams, tiles, n_views, B);
     if (s != TP_OK) return s;
-    return bind_workspace(B.n_tiles, B.n_pix, ws, ws_bytes, W);
+    return bind_workspace(cfg, B, ws, ws_bytes, W);
 }
 
 tp_status from_cuda(cudaError_t e)
@@ -293,6 +313,7 @@ tp_status do_backward(const tp_config *cfg, const tp_camera *cams, const int32_t
     tp_status s = batch_checks(cfg, cams, tiles, n_views, n, ws, ws_bytes, B, W);
     if (s != TP_OK) return s;
     if ((kept == nullptr) != (n_kept == nullptr)) return TP_ERR_INVALID_ARG;
+    if (kept && (cfg->flags & TP_COARSE_LAYERS)) return TP_ERR_UNSUPPORTED;
     if (!grad_pyramid) return TP_ERR_INVALID_ARG;
     if (n > 0 && (!records || !opacity || !desc || !grad_pos || !grad_size_w || !grad_opacity || !grad_desc ||
                   !aligned16(records)))
@@ -314,7 +335,7 @@ int64_t batch_workspace_bytes(const tp_config *cfg, const tp_camera *cams, const
     int64_t cap = entry_capacity > 0 ? entry_capacity : 8 * n_points * n_views;
     if (cap < 1) cap = 1;
     if (cap > 0x7FFFFFFF) cap = 0x7FFFFFFF;
-    return layout_for(B.n_tiles, B.n_pix, cap).end;
+    return layout_for(B.n_tiles, B.n_pix, coarse_slots(cfg, B), cap).end;
 }
 
 }  // namespace

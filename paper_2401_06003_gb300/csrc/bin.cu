@@ -15,8 +15,8 @@
 
 namespace tpk {
 
-// Calls fn(tile) for every screen tile the point's taps touch, at each of
-// its layers.  The taps and layers are exactly those of the blend kernels.
+// Calls fn(tile, L) for every screen tile the point's taps touch, at each of
+// its layers L.  The taps and layers are exactly those of the blend kernels.
 template <class Fn>
 __device__ __forceinline__ void for_each_tile(const Frame &F, const float4 &r, Fn &&fn)
 {
@@ -32,7 +32,7 @@ __device__ __forceinline__ void for_each_tile(const Frame &F, const float4 &r, F
         const int base = F.tile_base[L];
         const int tpr = F.tiles_x[L];
         for (int b = y0; b <= y1; ++b)
-            for (int a = x0; a <= x1; ++a) fn(base + b * tpr + a);
+            for (int a = x0; a <= x1; ++a) fn(base + b * tpr + a, L);
     }
 }
 
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kBlock) k_project_count(const __grid_constant_
         }
         rec[i] = r;
         const unsigned c = (unsigned)(i & (kCopies - 1));
-        for_each_tile(F, r, [&](int t) { atomicAdd(count + (size_t)t * kCopies + c, 1u); });
+        for_each_tile(F, r, [&](int t, int) { atomicAdd(count + (size_t)t * kCopies + c, 1u); });
     }
 }
 
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(int n_tiles, Workspace W)
     }
 }
 
-// Splat: every point appends its fragment key (z, i) and its blend payload
+// Splat: every point appends its fragment key (z, i, L) and its blend payload
 // (x, y, s, alpha) to the list of each tile it touches.
 template <int MaxV>
 __global__ void __launch_bounds__(kBlock) k_fill(const __grid_constant__ Batch<MaxV> B, Workspace W, long long n,
@@ -162,10 +162,10 @@ __global__ void __launch_bounds__(kBlock) k_fill(const __grid_constant__ Batch<M
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const float4 r = rec[i];
         if (!(r.z > 0.0f)) continue;  // culled
-        const unsigned long long key = frag_key(r.z, (unsigned)i);
         const float4 pay = make_float4(r.x, r.y, r.w, __ldg(opacity + i));
         const unsigned c = (unsigned)(i & (kCopies - 1));
-        for_each_tile(F, r, [&](int t) {
+        for_each_tile(F, r, [&](int t, int L) {
+            const unsigned long long key = frag_key(r.z, (unsigned)i, L);
             const unsigned e = tile_off[t] + atomicAdd(cursor + (size_t)t * kCopies + c, 1u);
             if (e < W.capacity) {
                 W.bucket_key[e] = key;

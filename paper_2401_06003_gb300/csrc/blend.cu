@@ -17,6 +17,14 @@
 // list, and the cost of a tile is linear in its fragments whatever their
 // arrival order.  The pixel then blends its list front to back (Eq. 6-7).
 //
+// With coarse-layer inclusion (Sec. 3.6, Implementation Details) the list of
+// pixel (L, j, k) also holds the fragments of every coarser pixel that
+// contains it.  That list is the pixel's own fragments plus the inclusive list
+// of its parent (L+1, j/2, k/2), and the K front-most of a union are among
+// the K front-most of each part, so the tiles run layer by layer, coarsest
+// first: each coarse pixel stores its kept list (keys and opacities) in the
+// workspace, and each child starts its own list from its parent's.
+//
 // The backward kernels run the adjoint of the blend per pixel back to front
 // over the kept list (division-free recurrence) and scatter the point
 // gradients with float atomics (one vector atomic per descriptor row).
@@ -235,7 +243,9 @@ struct TopK {
 
 // Builds the kept list of the thread's pixel (thread t owns pixel t of the
 // tile, t < tile_px); returns the kept count.  With count_all, *nfrag gets
-// the pixel's number of candidate fragments.
+// the pixel's number of candidate fragments in the tile's own list.  A
+// parent row prow >= 0 (coarse-layer inclusion) starts the list from the
+// parent pixel's kept list, which is sorted already.
 //
 // A tile whose list spans several chunks keeps, per pixel, the current K-th
 // key after each chunk: a later fragment at or behind it cannot enter the
@@ -245,14 +255,22 @@ struct TopK {
 // candidate counts are asked for, skip the thresholds.
 template <int K>
 __device__ int build_topk(const Frame &F, const Workspace &W, int tile, const TileGeom &g, const TileSmem &S,
-                          TopK<K> &top, bool count_all, unsigned *nfrag)
+                          TopK<K> &top, bool count_all, unsigned *nfrag, long long prow)
 {
     const int TP = F.tile_px, tid = threadIdx.x, NT = blockDim.x;
     const bool owner = tid < TP;
     top.clear();
+    if (prow >= 0) {
+#pragma unroll
+        for (int m = 0; m < K; ++m) {
+            top.key[m] = W.ckey[(long long)m * W.crows + prow];
+            top.e[m] = W.cgam[(long long)m * W.crows + prow];
+            top.n += top.key[m] != kEmptyKey ? 1 : 0;
+        }
+    }
     S.cnt[tid] = 0u;
     S.cur[tid] = 0u;
-    S.thr[tid] = kEmptyKey;
+    S.thr[tid] = top.key[K - 1];
     unsigned end = W.tile_off[tile + 1];
     if (end > W.capacity) end = W.capacity;
     unsigned beg = W.tile_off[tile];
@@ -364,26 +382,31 @@ __device__ __forceinline__ DescGroup<DescT> load_group(const DescT *__restrict__
 // are capped at 96 for K <= 16 so that five 128-thread CTAs fit on an SM
 // (the uncapped build of some instantiations takes 104 and fits four: the
 // 4K bf16 blend was 14% slower); K = 32 needs its registers for the list.
+// layer < 0: every tile of the batch; else the tiles of that layer (the
+// coarse-to-fine launches of coarse-layer inclusion).
 template <int K, typename DescT, int MaxV, bool STATS>
 __global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_blend(const __grid_constant__ Batch<MaxV> B, Workspace W,
                                              const DescT *__restrict__ desc,
                              float *__restrict__ pyramid, unsigned *__restrict__ kept,
                              unsigned char *__restrict__ n_kept, float *__restrict__ t_final,
-                             unsigned *__restrict__ n_frag)
+                             unsigned *__restrict__ n_frag, int layer)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (*((volatile unsigned *)W.status) & TP_FLAG_CAPACITY) return;  // the lists were cut short: outputs invalid
-    const int tile = blockIdx.x;  // global over the batch
+    const int tile = block_tile(B, layer);  // global over the batch
+    if (tile < 0) return;
     const int v = view_of_tile(B, tile);
     const Frame &F = B.view[v];
     const TileSmem S = carve(F, smem_raw);
     const TileGeom g = tile_geom(F, tile - B.tile_base[v]);
-    TopK<K> top;
-    unsigned nfr;
-    int nk = build_topk<K>(F, W, tile, g, S, top, STATS, &nfr);
     const int TP = F.tile_px, tid = threadIdx.x, L = g.L;
     const int j = g.x0 + tid % F.tile_w, k = g.y0 + tid / F.tile_w;
     const bool active = tid < TP && j < F.lw[L] && k < F.lh[L];
+    const bool parent = F.coarse && active && L + 1 < F.n_layers;
+    TopK<K> top;
+    unsigned nfr;
+    int nk = build_topk<K>(F, W, tile, g, S, top, STATS, &nfr,
+                           parent ? coarse_row(B, v, L + 1, j >> 1, k >> 1) : -1ll);
     if (!active) nk = 0;
     const int nk_warp = __reduce_max_sync(0xffffffffu, nk);
     const long long pix = B.pix_base[v] + F.pix_base[L] + (long long)k * F.lw[L] + j;
@@ -396,6 +419,14 @@ __global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_blend(const __grid_consta
             kmax = m < nk ? top.key[m] : kmax;
         }
         W.kmax[pix] = kmax;
+        if (F.coarse && L > 0) {  // the children of the next launch start from this list
+            const long long row = coarse_row(B, v, L, j, k);
+#pragma unroll
+            for (int m = 0; m < K; ++m) {
+                W.ckey[(long long)m * W.crows + row] = top.key[m];
+                W.cgam[(long long)m * W.crows + row] = top.e[m];
+            }
+        }
     }
     // front to back: weights T_m gamma_m (Eq. 6-7); gamma came with the key.
     // Descriptor loads go out four slots at a time; unused slots read
@@ -413,6 +444,10 @@ __global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_blend(const __grid_consta
             T = T * (1.0f - gam);
         }
     }
+    // descriptor rows of the kept points (empty slots: row 0); the keys are dead from here
+    unsigned row[K];
+#pragma unroll
+    for (int m = 0; m < K; ++m) row[m] = m < nk ? key_point(top.key[m]) : 0u;
     const int D = F.D;
     constexpr int G = DescGroup<DescT>::G;
     for (int d0 = 0; d0 < D; d0 += G) {
@@ -425,8 +460,7 @@ __global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_blend(const __grid_consta
             DescGroup<DescT> t[NB];
 #pragma unroll
             for (int u = 0; u < NB; ++u)
-                t[u] = load_group(desc, m0 + u < nk ? (unsigned)(top.key[m0 + u] & 0xFFFFFFFFull) : 0u, D, d0,
-                                  F.desc_vec);
+                t[u] = load_group(desc, row[m0 + u], D, d0, F.desc_vec);
 #pragma unroll
             for (int u = 0; u < NB; ++u) {
                 if (m0 + u < nk) {
@@ -450,11 +484,16 @@ __global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_blend(const __grid_consta
     if (kept) {
 #pragma unroll
         for (int m = 0; m < K; ++m)
-            kept[pix * K + m] = m < nk ? (unsigned)(top.key[m] & 0xFFFFFFFFull) : kNoPoint;
+            kept[pix * K + m] = m < nk ? row[m] : kNoPoint;
     }
     if (n_kept) n_kept[pix] = (unsigned char)nk;
     if (t_final) t_final[pix] = T;
-    if (STATS) n_frag[pix] = nfr;
+    if (STATS) {
+        // the parent's count, from the previous launch, covers every coarser layer
+        if (parent)
+            nfr += n_frag[B.pix_base[v] + F.pix_base[L + 1] + (long long)(k >> 1) * F.lw[L + 1] + (j >> 1)];
+        n_frag[pix] = nfr;
+    }
 }
 
 constexpr int kMaxGradD = 64;
@@ -520,14 +559,18 @@ __device__ __forceinline__ void adjoint_fragment(const Frame &F, int L, int j, i
 // is not larger, so one pass over the tile's entries drops every kept
 // fragment into one of its pixel's K slots (no selection work), each pixel's
 // thread sorts its at most K slots, and runs the adjoint of its blend back to
-// front in a rolled loop.
+// front in a rolled loop.  With coarse-layer inclusion the pixel's other kept
+// fragments are the entries of its parent's stored list up to the same key;
+// their payload comes from the point records, and their gradients from their
+// own layer's pixel (each key carries its layer).
 // Registers are capped at 96 for K <= 16 (five 128-thread CTAs per SM); the
 // kept slots are sorted in shared memory, so no register list is live.
 template <int K, typename DescT, int MaxV, int DC>
 __global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_backward(const __grid_constant__ Batch<MaxV> B, Workspace W,
                                                           const DescT *__restrict__ desc,
                                 const float *__restrict__ grad_pyr, float *__restrict__ gpos, float *__restrict__ gsw,
-                                float *__restrict__ gop, float *__restrict__ gdesc)
+                                float *__restrict__ gop, float *__restrict__ gdesc, long long n,
+                                const float4 *__restrict__ rec_all, const float *__restrict__ opacity)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (*((volatile unsigned *)W.status) & TP_FLAG_CAPACITY) return;  // the lists were cut short: outputs invalid
@@ -568,8 +611,23 @@ __global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_backward(const __grid_con
     __syncthreads();
     if (!active) return;
     int nk = (int)S.cnt[tid];
+    if (F.coarse && L + 1 < F.n_layers) {
+        const long long prow = coarse_row(B, v, L + 1, j >> 1, k >> 1);
+        const unsigned long long km = thr[tid];
+        for (int m = 0; m < K; ++m) {
+            const unsigned long long key = W.ckey[(long long)m * W.crows + prow];
+            if (key > km) break;  // the stored list is sorted; empty slots hold the largest key
+            if (nk < K) {
+                kk[nk * TP + tid] = key;
+                ke[nk * TP + tid] = kNoPoint;
+                kt[nk * TP + tid] = __uint_as_float(W.cgam[(long long)m * W.crows + prow]);
+            }
+            ++nk;
+        }
+    }
     if (nk > K) nk = K;
     if (nk == 0) return;
+    const float4 *__restrict__ rec = rec_all + (long long)v * n;
     // insertion sort of the pixel's slots (at most K) by key, in its own
     // shared-memory column (no registers held for the list)
     for (int a = 1; a < nk; ++a) {
@@ -611,14 +669,22 @@ __global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_backward(const __grid_con
         for (int u = 0; u < NB; ++u) {
             const int m = m1 - u >= 0 ? m1 - u : 0;
             key[u] = kk[m * TP + tid];
-            pay[u] = W.bucket_pay[ke[m * TP + tid]];
-            t0[u] = load_group(desc, (unsigned)(key[u] & 0xFFFFFFFFull), D, 0, F.desc_vec);
+            const unsigned ent = ke[m * TP + tid];
+            if (ent != kNoPoint) {
+                pay[u] = W.bucket_pay[ent];
+            } else {  // a coarser layer's fragment
+                const unsigned i = key_point(key[u]);
+                const float4 r = rec[i];
+                pay[u] = make_float4(r.x, r.y, r.w, __ldg(opacity + i));
+            }
+            t0[u] = load_group(desc, key_point(key[u]), D, 0, F.desc_vec);
         }
 #pragma unroll
         for (int u = 0; u < NB; ++u) {
             const int m = m1 - u;
             if (m < 0) break;
-            adjoint_fragment<DescT, DC>(F, L, j, k, (unsigned)(key[u] & 0xFFFFFFFFull), pay[u].x, pay[u].y,
+            const int Lf = key_layer(key[u]), d = Lf - L;  // the fragment's own layer and pixel
+            adjoint_fragment<DescT, DC>(F, Lf, j >> d, k >> d, key_point(key[u]), pay[u].x, pay[u].y,
                                     __uint_as_float((unsigned)(key[u] >> 32)), pay[u].z, pay[u].w, kt[m * TP + tid],
                                     G, R, t0[u], desc, gpos, gsw, gop, gdesc);
         }
@@ -705,34 +771,51 @@ static size_t batch_smem(const Batch<MaxV> &B)
     return region + (3 * (size_t)B.max_threads + 32) * sizeof(unsigned) + 8 * (size_t)B.max_threads;
 }
 
+// One launch over every tile, or with coarse-layer inclusion one launch per
+// layer, coarsest first (each layer reads the lists its parent layer stored).
+template <int K, typename DescT, int MaxV, bool STATS>
+static cudaError_t blend_launches(const Batch<MaxV> &B, const Workspace &W, const DescT *desc, float *pyramid,
+                                  unsigned *kept, unsigned char *n_kept, float *t_final, unsigned *n_frag,
+                                  cudaStream_t stream)
+{
+    const size_t smem = batch_smem(B);
+    cudaError_t e = prepare_tile_kernel(k_tile_blend<K, DescT, MaxV, STATS>, smem, B.max_threads);
+    if (e != cudaSuccess) return e;
+    if (!B.view[0].coarse) {
+        k_tile_blend<K, DescT, MaxV, STATS><<<B.n_tiles, B.max_threads, smem, stream>>>(
+            B, W, desc, pyramid, kept, n_kept, t_final, n_frag, -1);
+        return cudaGetLastError();
+    }
+    for (int L = B.view[0].n_layers - 1; L >= 0; --L) {
+        int tiles = 0;
+        for (int v = 0; v < B.n_views; ++v) tiles += B.view[v].tile_base[L + 1] - B.view[v].tile_base[L];
+        if (tiles == 0) continue;
+        k_tile_blend<K, DescT, MaxV, STATS><<<tiles, B.max_threads, smem, stream>>>(
+            B, W, desc, pyramid, kept, n_kept, t_final, n_frag, L);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 template <int K, typename DescT, int MaxV>
 static cudaError_t blend_impl(const Batch<MaxV> &B, const Workspace &W, const void *desc, float *pyramid,
                               unsigned *kept, unsigned char *n_kept, float *t_final, unsigned *n_frag,
                               cudaStream_t stream)
 {
-    const size_t smem = batch_smem(B);
-    if (n_frag) {
-        cudaError_t e = prepare_tile_kernel(k_tile_blend<K, DescT, MaxV, true>, smem, B.max_threads);
-        if (e != cudaSuccess) return e;
-        k_tile_blend<K, DescT, MaxV, true><<<B.n_tiles, B.max_threads, smem, stream>>>(
-            B, W, static_cast<const DescT *>(desc), pyramid, kept, n_kept, t_final, n_frag);
-    } else {
-        cudaError_t e = prepare_tile_kernel(k_tile_blend<K, DescT, MaxV, false>, smem, B.max_threads);
-        if (e != cudaSuccess) return e;
-        k_tile_blend<K, DescT, MaxV, false><<<B.n_tiles, B.max_threads, smem, stream>>>(
-            B, W, static_cast<const DescT *>(desc), pyramid, kept, n_kept, t_final, n_frag);
-    }
-    return cudaGetLastError();
+    const DescT *d = static_cast<const DescT *>(desc);
+    if (n_frag) return blend_launches<K, DescT, MaxV, true>(B, W, d, pyramid, kept, n_kept, t_final, n_frag, stream);
+    return blend_launches<K, DescT, MaxV, false>(B, W, d, pyramid, kept, n_kept, t_final, n_frag, stream);
 }
 
 template <int K, typename DescT, int MaxV, int DC>
 static cudaError_t backward_launch(const Batch<MaxV> &B, const Workspace &W, const DescT *d, const float *grad_pyr,
-                                   float *gpos, float *gsw, float *gop, float *gdesc, size_t smem, cudaStream_t stream)
+                                   float *gpos, float *gsw, float *gop, float *gdesc, long long n, const float4 *rec,
+                                   const float *opacity, size_t smem, cudaStream_t stream)
 {
     cudaError_t e = prepare_tile_kernel(k_tile_backward<K, DescT, MaxV, DC>, smem, B.max_threads);
     if (e != cudaSuccess) return e;
     k_tile_backward<K, DescT, MaxV, DC><<<B.n_tiles, B.max_threads, smem, stream>>>(B, W, d, grad_pyr, gpos, gsw,
-                                                                                     gop, gdesc);
+                                                                                     gop, gdesc, n, rec, opacity);
     return cudaGetLastError();
 }
 
@@ -755,11 +838,15 @@ static cudaError_t backward_impl(const Batch<MaxV> &B, const Workspace &W, long 
     // the common descriptor widths get compile-time instantiations (K = 16)
     if constexpr (K == 16) {
         const int D = B.view[0].D;
-        if (D == 4) return backward_launch<K, DescT, MaxV, 4>(B, W, d, grad_pyr, gpos, gsw, gop, gdesc, smem, stream);
+        if (D == 4)
+            return backward_launch<K, DescT, MaxV, 4>(B, W, d, grad_pyr, gpos, gsw, gop, gdesc, n, rec, opacity, smem,
+                                                      stream);
         if (D == 16)
-            return backward_launch<K, DescT, MaxV, 16>(B, W, d, grad_pyr, gpos, gsw, gop, gdesc, smem, stream);
+            return backward_launch<K, DescT, MaxV, 16>(B, W, d, grad_pyr, gpos, gsw, gop, gdesc, n, rec, opacity,
+                                                       smem, stream);
     }
-    return backward_launch<K, DescT, MaxV, 0>(B, W, d, grad_pyr, gpos, gsw, gop, gdesc, smem, stream);
+    return backward_launch<K, DescT, MaxV, 0>(B, W, d, grad_pyr, gpos, gsw, gop, gdesc, n, rec, opacity, smem,
+                                              stream);
 }
 
 #define TPK_DISPATCH_K(KVAL, ...)                                   \

@@ -36,6 +36,8 @@ struct Frame {
     int chunk;             // tile-list entries merged per chunk by the tile kernels
     int desc_vec;          // 1 if descriptors can be read 4 channels at a time
     int grad_vec;          // 1 if descriptor gradients can take 4-channel vector atomics
+    int coarse;            // 1: coarse-layer inclusion (a pixel's list also holds the fragments of
+                           //    the coarser-layer pixels that contain it, Sec. 3.6)
     int lw[kMaxLayers], lh[kMaxLayers];            // layer sizes W_L, H_L
     int tiles_x[kMaxLayers], tiles_y[kMaxLayers];  // tiles per layer row / column
     int tile_base[kMaxLayers + 1];                 // first tile id of each layer
@@ -57,8 +59,33 @@ struct Batch {
     int max_threads;      // largest tile CTA over the views
     int tile_base[MaxV + 1];
     long long pix_base[MaxV + 1];
+    long long cpix_base[MaxV + 1];  // first coarse-list row of each view (pixels of layers >= 1)
     Frame view[MaxV];
 };
+
+// Row of the coarse-list arrays of pixel (j, k) of layer L >= 1 of view v.
+template <int MaxV>
+__device__ __forceinline__ long long coarse_row(const Batch<MaxV> &B, int v, int L, int j, int k)
+{
+    const Frame &F = B.view[v];
+    return B.cpix_base[v] + (F.pix_base[L] - F.pix_base[1]) + (long long)k * F.lw[L] + j;
+}
+
+// The tile of CTA blockIdx.x: every tile of the batch in order (layer < 0), or
+// the tiles of one layer, view after view.
+template <int MaxV>
+__device__ __forceinline__ int block_tile(const Batch<MaxV> &B, int layer)
+{
+    int c = (int)blockIdx.x;
+    if (layer < 0) return c;
+    for (int v = 0; v < B.n_views; ++v) {
+        const Frame &F = B.view[v];
+        const int nt = F.tile_base[layer + 1] - F.tile_base[layer];
+        if (c < nt) return B.tile_base[v] + F.tile_base[layer] + c;
+        c -= nt;
+    }
+    return -1;
+}
 
 template <int MaxV>
 __device__ __forceinline__ int view_of_tile(const Batch<MaxV> &B, int tile)
@@ -92,6 +119,12 @@ struct Workspace {
     unsigned long long *bucket_key;  // [capacity] fragment key (z bits, point index) of each entry
     float4 *bucket_pay;     // [capacity] (x, y, s, alpha) of the entry's point
     unsigned long long *kmax;  // [P] largest kept key of each pixel (0: none), written by the blend
+    // coarse-layer inclusion only: the kept list of every pixel of layers >= 1
+    // (keys, then fragment opacities gamma as float bits), slot-major:
+    // slot m of coarse row c at [m * crows + c]; empty slots hold kEmptyKey
+    unsigned long long *ckey;
+    unsigned *cgam;
+    long long crows;
     unsigned capacity;
 };
 
@@ -244,11 +277,16 @@ __device__ __forceinline__ bool tap_tile_range(const AxisTaps &t, int tile, int 
 }
 
 // Sort key of a fragment: depth bits (z > 0, so the bits order like the
-// values) above the point index, which breaks ties.
-__device__ __forceinline__ unsigned long long frag_key(float z, unsigned i)
+// values) above the point index, which breaks ties, above the fragment's own
+// pyramid layer (4 bits), which orders a point's two layers in a list that
+// holds both (coarse-layer inclusion), the finer first.  Point indices stay
+// below 2^27, so the low word holds index and layer.
+__device__ __forceinline__ unsigned long long frag_key(float z, unsigned i, int L)
 {
-    return ((unsigned long long)__float_as_uint(z) << 32) | (unsigned long long)i;
+    return ((unsigned long long)__float_as_uint(z) << 32) | (unsigned long long)((i << 4) | (unsigned)L);
 }
+__device__ __forceinline__ unsigned key_point(unsigned long long key) { return (unsigned)(key & 0xFFFFFFFFull) >> 4; }
+__device__ __forceinline__ int key_layer(unsigned long long key) { return (int)(key & 15ull); }
 
 __device__ __forceinline__ int tile_layer(const Frame &F, int tile)
 {

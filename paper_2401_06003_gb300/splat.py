@@ -50,10 +50,14 @@ class Renderer:
     ``mode``: "recompute" keeps only the tile lists between the forward and
     the backward pass and rebuilds each pixel's sorted list in the backward
     kernel; "store" keeps the per-pixel kept lists from the forward pass.
+    ``coarse``: coarse-layer inclusion (Sec. 3.6): each pixel's list also
+    holds the fragments of the coarser pixels that contain it (backward
+    passes in "recompute" mode only).
     """
 
     def __init__(self, camera, n_layers: int, K: int = 16, D: int = 4, eps: float = 0.25,
-                 desc_dtype=torch.float32, mode: str = "recompute", tile=(16, 8), device=None):
+                 desc_dtype=torch.float32, mode: str = "recompute", tile=(16, 8), device=None,
+                 coarse: bool = False):
         self.lib = _lib.load()
         self.camera = camera
         self.cam = _lib.make_camera(camera)
@@ -61,7 +65,9 @@ class Renderer:
             raise ValueError(f"descriptor dtype {desc_dtype} not supported")
         self.desc_dtype = desc_dtype
         self.mode = {"store": _lib.TP_STORE_LISTS, "recompute": _lib.TP_RECOMPUTE}[mode]
-        self.cfg = _lib.make_config(n_layers, K, D, eps, _DTYPES[desc_dtype], self.mode, tile[0], tile[1])
+        self.coarse = bool(coarse)
+        self.cfg = _lib.make_config(n_layers, K, D, eps, _DTYPES[desc_dtype], self.mode, tile[0], tile[1],
+                                    _lib.TP_COARSE_LAYERS if coarse else 0)
         self.n_layers, self.K, self.D = int(n_layers), int(K), int(D)
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         offs = (ctypes.c_int64 * (n_layers + 1))()
@@ -242,7 +248,7 @@ class BatchRenderer:
     """
 
     def __init__(self, cameras, n_layers: int, K: int = 16, D: int = 4, eps: float = 0.25,
-                 desc_dtype=torch.float32, mode: str = "recompute", tiles=None, device=None):
+                 desc_dtype=torch.float32, mode: str = "recompute", tiles=None, device=None, coarse: bool = False):
         self.lib = _lib.load()
         self.cameras = list(cameras)
         V = len(self.cameras)
@@ -255,7 +261,9 @@ class BatchRenderer:
             raise ValueError(f"descriptor dtype {desc_dtype} not supported")
         self.desc_dtype = desc_dtype
         self.mode = {"store": _lib.TP_STORE_LISTS, "recompute": _lib.TP_RECOMPUTE}[mode]
-        self.cfg = _lib.make_config(n_layers, K, D, eps, _DTYPES[desc_dtype], self.mode)
+        self.coarse = bool(coarse)
+        self.cfg = _lib.make_config(n_layers, K, D, eps, _DTYPES[desc_dtype], self.mode,
+                                    flags=_lib.TP_COARSE_LAYERS if coarse else 0)
         self.n_layers, self.K, self.D = int(n_layers), int(K), int(D)
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         offs = (ctypes.c_int64 * (V + 1))()

@@ -31,15 +31,15 @@ def to_dev(a, dtype=torch.float32):
 
 
 def gpu_frame(scene, view=0, K=None, mode="store", tile=(16, 8), desc_dtype=torch.float32, desc=None,
-              capacity=0, pos=None, expect_flags=0):
+              capacity=0, pos=None, expect_flags=0, coarse=False, camera=None):
     """Render one view on the GPU with every optional output; numpy results.
 
     The device status flags must equal ``expect_flags`` (None: not checked)."""
-    cam = scene.cameras[view]
+    cam = scene.cameras[view] if camera is None else camera
     K = K or scene.K
     d = scene.desc if desc is None else desc
     r = Renderer(cam, scene.n_layers, K=K, D=d.shape[1], desc_dtype=desc_dtype, mode=mode, tile=tile,
-                 device=device())
+                 device=device(), coarse=coarse)
     t_pos = to_dev(scene.pos if pos is None else pos)
     t_sw = to_dev(scene.size_w)
     t_op = to_dev(scene.opacity)

@@ -31,7 +31,31 @@ def test_exports_every_declared_symbol(lib):
 
 def test_struct_layout_matches_header():
     assert ctypes.sizeof(_lib.tp_camera) == 17 * 4 + 2 * 4
-    assert ctypes.sizeof(_lib.tp_config) == 8 * 4
+    assert ctypes.sizeof(_lib.tp_config) == 9 * 4
+
+
+def test_coarse_layer_flag(lib):
+    """Coarse-layer inclusion adds K slots (8-byte key, 4-byte opacity) per
+    pixel of layers >= 1 to the workspace; unknown flag bits are refused; a
+    stored-lists backward with inclusion is refused before any CUDA call."""
+    sc = scenes.make_config("cube20k_256", n=10)
+    cam = _lib.make_camera(sc.camera)
+    offs, _, _ = oracle.pyramid_layout(sc.camera.width, sc.camera.height, 4)
+    coarse_pix = int(offs[-1] - offs[1])
+    for K in (4, 16, 32):
+        plain = _lib.make_config(4, K, 4)
+        coarse = _lib.make_config(4, K, 4, flags=_lib.TP_COARSE_LAYERS)
+        a = lib.tp_workspace_bytes(ctypes.byref(plain), ctypes.byref(cam), 1000, 0)
+        b = lib.tp_workspace_bytes(ctypes.byref(coarse), ctypes.byref(cam), 1000, 0)
+        assert 0 <= (b - a) - 12 * K * coarse_pix < 512, (K, a, b)
+    bad = _lib.make_config(4, 16, 4, flags=0x2)
+    assert lib.tp_workspace_bytes(ctypes.byref(bad), ctypes.byref(cam), 10, 0) == -1
+    coarse = _lib.make_config(4, 16, 4, mode=_lib.TP_STORE_LISTS, flags=_lib.TP_COARSE_LAYERS)
+    need = lib.tp_workspace_bytes(ctypes.byref(coarse), ctypes.byref(cam), 10, 0)
+    fake = ctypes.c_void_p(1 << 20)  # never dereferenced: the call fails in its host checks
+    st = lib.tp_splat_backward(ctypes.byref(coarse), ctypes.byref(cam), 10, fake, fake, fake, fake, fake, fake,
+                               fake, fake, fake, fake, fake, need, None)
+    assert st == _lib.TP_ERR_UNSUPPORTED
 
 
 @pytest.mark.parametrize("W,H,L", [(256, 256, 4), (1920, 1080, 8), (257, 131, 3), (3840, 2160, 10), (1, 1, 1)])

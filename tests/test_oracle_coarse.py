@@ -198,3 +198,22 @@ def test_coarse_adjoint_matches_frame_differences():
             assert abs(ad - fd) <= 2e-4 * max(1.0, abs(fd)), (i, what, ad, fd)
             checked += 1
     assert checked > 60
+
+
+def test_point_selection_covers_the_coarse_lists():
+    """A frame over selected points holds every list their fragments join
+    (with inclusion, also the finer pixels below a coarse fragment), so their
+    gradients equal those of the whole frame."""
+    pos, sw, alpha, desc, cam, W, H = _tiny(6, n=60, W=40, H=36)
+    n_layers, K = 5, 6
+    G = np.random.default_rng(7).uniform(-1, 1, (int(oracle.pyramid_layout(W, H, n_layers)[0][-1]), 3))
+    full = oracle.Frame(cam, W, H, n_layers, K, pos, sw, alpha, desc, prec32=False, coarse=True)
+    g_full = full.backward(G)
+    pts = np.arange(0, 60, 7)
+    sub = oracle.Frame(cam, W, H, n_layers, K, pos, sw, alpha, desc, prec32=False, coarse=True, points=pts)
+    rows = sub.pixels()
+    g_sub = sub.backward(G[rows])
+    plain_rows = oracle.Frame(cam, W, H, n_layers, K, pos, sw, alpha, desc, prec32=False, points=pts).pixels()
+    assert len(rows) > len(plain_rows), "coarse fragments must add finer pixels"
+    for k in ("pos", "size_w", "opacity", "desc"):
+        np.testing.assert_allclose(g_sub[k][pts], g_full[k][pts], rtol=1e-12, atol=1e-14)
