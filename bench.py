@@ -304,7 +304,7 @@ def run_ours(args):
     ws = r.new_workspace(N)
     rec = torch.empty((N, 4), dtype=torch.float32, device=dev)
     pyr = torch.empty((P, D), dtype=torch.float32, device=dev)
-    grads = (torch.empty((N, 3), device=dev), torch.empty((N,), device=dev), torch.empty((N,), device=dev),
+    grads = (torch.empty((N, 4), device=dev), None, torch.empty((N,), device=dev),  # packed (X, Y, Z, s_w) rows
              torch.empty((N, D), device=dev))
     store = args.mode == "store"
     stream = torch.cuda.current_stream(dev)
@@ -391,8 +391,9 @@ def run_ours(args):
         # the host copy of the cloud is stored in the same (relabeled) order
         h_in = [t.cpu().pin_memory() for t in (pos, sw, op, desc)]
         d_in = [[pos, sw, op, desc], [torch.empty_like(t) for t in (pos, sw, op, desc)]]
-        d_gr = [list(grads), [torch.empty_like(g) for g in grads]]
-        h_out = [[torch.empty(g.shape, dtype=torch.float32).pin_memory() for g in grads] for _ in range(2)]
+        d_gr = [list(grads), [None if g is None else torch.empty_like(g) for g in grads]]
+        h_out = [[torch.empty(g.shape, dtype=torch.float32).pin_memory() for g in grads if g is not None]
+                 for _ in range(2)]
         h2d = sum(t.numel() * t.element_size() for t in h_in)
         d2h = sum(t.numel() * t.element_size() for t in h_out[0])
         s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
@@ -420,7 +421,7 @@ def run_ours(args):
                 computed[b].record(stream)
                 s_out.wait_event(computed[b])
                 with torch.cuda.stream(s_out):
-                    for h_, g_ in zip(h_out[b], d_gr[b]):
+                    for h_, g_ in zip(h_out[b], [g for g in d_gr[b] if g is not None]):
                         h_.copy_(g_, non_blocking=True)
                     downloaded[b].record(s_out)
             stream.wait_stream(s_out)
@@ -645,7 +646,7 @@ def run_batch(args):
     gen = torch.Generator(device=dev)
     gen.manual_seed(4321 + rank)
     G = (torch.rand((br.P, D), generator=gen, device=dev) * 2 - 1).contiguous()
-    grads = (torch.empty((N, 3), device=dev), torch.empty((N,), device=dev), torch.empty((N,), device=dev),
+    grads = (torch.empty((N, 4), device=dev), None, torch.empty((N,), device=dev),  # packed (X, Y, Z, s_w) rows
              torch.empty((N, D), device=dev))
 
     def step():

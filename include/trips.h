@@ -114,13 +114,18 @@ typedef enum {
     TP_ERR_NONFINITE = 3,   /* a point had a non-finite input or s_w < 0; it was culled */
     TP_ERR_TIMEOUT = 4,     /* a bounded device wait gave up (no current kernel waits on the device) */
     TP_ERR_CUDA = 5,        /* a CUDA runtime call or launch failed */
-    TP_ERR_UNSUPPORTED = 6  /* valid but not supported by this build (e.g. K) */
+    TP_ERR_UNSUPPORTED = 6, /* valid but not supported by this build (e.g. K) */
+    TP_ERR_BOUNDS = 7       /* checking build only: a kernel computed an out-of-range index */
 } tp_status;
 
-/* Bits of the device status word (tp_get_status). */
+/* Bits of the device status word (tp_get_status).  TP_FLAG_BOUNDS is set
+ * only by the checking build (libtrips_debug.so, compiled with TP_DEBUG),
+ * whose kernels test every list, pyramid, workspace and shared-memory index
+ * they compute and skip an out-of-range access instead of making it. */
 #define TP_FLAG_NONFINITE 0x1u
 #define TP_FLAG_CAPACITY 0x2u
 #define TP_FLAG_TIMEOUT 0x4u
+#define TP_FLAG_BOUNDS 0x8u
 
 /* Pinhole camera; R is row-major world->camera, X_c = R X_w + t. */
 typedef struct {
@@ -228,7 +233,10 @@ TP_API tp_status tp_blend(const tp_config *cfg, const tp_camera *cam, int64_t n,
  * Sec. 3.5).  Given G = dL/dpyramid [P][D] (device), writes
  *   grad_pos [n][3], grad_size_w [n], grad_opacity [n], grad_desc [n][D]
  * (device float32, overwritten; every entry, zero where a point has no kept
- * fragment).  With kept and n_kept (TP_STORE_LISTS) the per-pixel lists come
+ * fragment).  With grad_size_w == NULL the position and size gradients are
+ * packed: grad_pos is [n][4] rows (dL/dX, dL/dY, dL/dZ, dL/ds_w), 16-byte
+ * aligned, and each kept fragment adds to its point's row with one 16-byte
+ * atomic instead of four scalar ones (the same for the batch calls).  With kept and n_kept (TP_STORE_LISTS) the per-pixel lists come
  * from tp_blend.  With kept == NULL (TP_RECOMPUTE) the lists are rebuilt from
  * the workspace's tile lists and the per-pixel largest kept key that
  * tp_blend leaves in the workspace (8 bytes per pixel); the workspace must
@@ -254,7 +262,8 @@ TP_API tp_status tp_splat_backward(const tp_config *cfg, const tp_camera *cam, i
  *   dL/dcx = sum Gx,  dL/dcy = sum Gy,  dL/dt = sum dL/dX_c,
  *   dL/dR[r][c] = sum dL/dX_c[r] X_w[c]   (sums over the visible points).
  *   pos [n][3], records [n][4] (this view's tp_project output, 16-byte
- *   aligned), grad_pos [n][3], grad_size_w [n]: device, read.  The point
+ *   aligned), grad_pos [n][3], grad_size_w [n]: device, read (grad_size_w
+ *   NULL: grad_pos is the packed [n][4] layout of tp_splat_backward).  The point
  *   gradients must come from a backward pass of this view alone (the batched
  *   backward sums the views' gradients).
  *   grad_camera [16] (device, float64, overwritten): dL/d(fx, fy, cx, cy,
@@ -388,6 +397,28 @@ TP_API tp_status tp_batch_splat_backward(const tp_config *cfg, const tp_camera *
                                          float *grad_opacity, float *grad_desc, void *ws, int64_t ws_bytes,
                                          tp_stream_t stream);
 
+/*
+ * The batch backward (lists recomputed) that also returns the gradient of
+ * every view's camera, as the paper optimises all training cameras with the
+ * points (Sec. 3.5).  Point gradients are those of tp_batch_splat_backward
+ * (summed over the views); grad_cameras [n_views][16] (device, float64,
+ * written) holds per view dL/d(fx, fy, cx, cy, R[0..8], t[0..2]) in the
+ * order and meaning of tp_camera_backward, accumulated per fragment from its
+ * screen-space gradient (dL/dx, dL/dy, dL/ds), its camera-space gradient
+ * dL/dX_c and the point's world position pos [n][3] (device, read):
+ *   dL/dfx += (dL/dx (x - cx) + dL/ds s) / fx,  dL/dfy += dL/dy (y - cy) / fy,
+ *   dL/dcx += dL/dx,  dL/dcy += dL/dy,  dL/dt += dL/dX_c,
+ *   dL/dR[a][b] += dL/dX_c[a] X_w[b].
+ * Float32 per-CTA sums, added into float64 with one atomic each.  Returns
+ * TP_ERR_INVALID_ARG when grad_cameras or (for n > 0) pos is NULL.
+ */
+TP_API tp_status tp_batch_splat_backward_cameras(const tp_config *cfg, const tp_camera *cams, const int32_t *tiles,
+                                                 int32_t n_views, int64_t n, const float *pos, const float *records,
+                                                 const float *opacity, const void *desc, const float *grad_pyramid,
+                                                 float *grad_pos, float *grad_size_w, float *grad_opacity,
+                                                 float *grad_desc, double *grad_cameras, void *ws, int64_t ws_bytes,
+                                                 tp_stream_t stream);
+
 /* ------------------------------------------------------------------------
  * Forward render with no caller workspace.  The paper has no counterpart:
  * this entry point exists for callers that may not allocate device memory
@@ -433,7 +464,7 @@ TP_API tp_status tp_render_forward_static(const tp_config *cfg, const tp_camera 
 /*
  * Synchronises `stream` and reads the workspace's device status word into
  * *device_flags (host; TP_FLAG_* bits).  Returns TP_ERR_CAPACITY,
- * TP_ERR_TIMEOUT or TP_ERR_NONFINITE for the first set bit in that order,
+ * TP_ERR_BOUNDS, TP_ERR_TIMEOUT or TP_ERR_NONFINITE for the first set bit in that order,
  * TP_OK if none is set.
  */
 TP_API tp_status tp_get_status(const void *ws, tp_stream_t stream, int32_t *device_flags);

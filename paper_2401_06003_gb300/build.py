@@ -3,6 +3,12 @@
 Each .cu under csrc/ is compiled by nvcc in parallel, then linked into
 ``paper_2401_06003_gb300/_build/libtrips.so`` with the CUDA runtime linked
 statically, so loading the library needs no GPU driver.
+
+``build(debug=True)`` makes the checking variant
+``paper_2401_06003_gb300/_build_debug/libtrips_debug.so`` from the same
+sources with TP_DEBUG defined: every list, pyramid, workspace and
+shared-memory index the kernels compute is checked before use, and an
+out-of-range one skips the access and sets TP_FLAG_BOUNDS in the status word.
 """
 from __future__ import annotations
 
@@ -19,6 +25,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libtrips.so")
+BUILD_DEBUG = os.path.join(PKG, "_build_debug")
+LIB_DEBUG = os.path.join(BUILD_DEBUG, "libtrips_debug.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
@@ -61,23 +69,27 @@ def source_hash(files=None) -> str:
     return h.hexdigest()[:16]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Compile and link libtrips.so if any source is newer; returns its path."""
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, debug: bool = False) -> str:
+    """Compile and link libtrips.so (or, with debug, libtrips_debug.so) if any
+    source is newer; returns its path."""
+    out_dir, lib = (BUILD_DEBUG, LIB_DEBUG) if debug else (BUILD, LIB)
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     cc = nvcc()
     extra = ["-Xptxas", "-v"] if ptxas_info else []
+    if debug:
+        extra.append("-DTP_DEBUG")
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src) + ".o")
         cmd = [cc, *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -90,13 +102,21 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         for _, log in results:
             if log:
                 sys.stderr.write(log)
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     cmd = [cc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *[o for o, _ in results]]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
+
+
+def build_all(force: bool = False) -> tuple[str, str]:
+    """Both variants, compiled concurrently: (libtrips.so, libtrips_debug.so)."""
+    with concurrent.futures.ThreadPoolExecutor(max_workers=2) as ex:
+        rel = ex.submit(build, force)
+        dbg = ex.submit(build, force, debug=True)
+        return rel.result(), dbg.result()
 
 
 if __name__ == "__main__":

@@ -225,7 +225,9 @@ tp_status batch_checks(const tp_config *cfg, const tp_camera *cams, const int32_
     if (n * (int64_t)(n_views > 0 ? n_views : 1) * 8 >= ((int64_t)1 << 32)) return TP_ERR_INVALID_ARG;
     tp_status s = make_batch(cfg, cams, tiles, n_views, B);
     if (s != TP_OK) return s;
-    return bind_workspace(cfg, B, ws, ws_bytes, W);
+    s = bind_workspace(cfg, B, ws, ws_bytes, W);
+    W.n_points = n;
+    return s;
 }
 
 tp_status from_cuda(cudaError_t e)
@@ -306,22 +308,27 @@ template <int MaxV>
 tp_status do_backward(const tp_config *cfg, const tp_camera *cams, const int32_t *tiles, int n_views, int64_t n,
                       const float *records, const float *opacity, const void *desc, const uint32_t *kept,
                       const uint8_t *n_kept, const float *grad_pyramid, float *grad_pos, float *grad_size_w,
-                      float *grad_opacity, float *grad_desc, void *ws, int64_t ws_bytes, tp_stream_t stream)
+                      float *grad_opacity, float *grad_desc, void *ws, int64_t ws_bytes, tp_stream_t stream,
+                      const float *pos = nullptr, double *grad_cameras = nullptr)
 {
     Batch<MaxV> B;
     Workspace W;
     tp_status s = batch_checks(cfg, cams, tiles, n_views, n, ws, ws_bytes, B, W);
     if (s != TP_OK) return s;
     if ((kept == nullptr) != (n_kept == nullptr)) return TP_ERR_INVALID_ARG;
+    if (grad_cameras && (kept || (n > 0 && !pos))) return TP_ERR_INVALID_ARG;
     if (kept && (cfg->flags & TP_COARSE_LAYERS)) return TP_ERR_UNSUPPORTED;
     if (!grad_pyramid) return TP_ERR_INVALID_ARG;
-    if (n > 0 && (!records || !opacity || !desc || !grad_pos || !grad_size_w || !grad_opacity || !grad_desc ||
-                  !aligned16(records)))
+    // grad_size_w NULL: grad_pos holds packed [n][4] rows (X, Y, Z, s_w), 16-byte aligned
+    const bool pos4 = grad_size_w == nullptr;
+    if (n > 0 && (!records || !opacity || !desc || !grad_pos || !grad_opacity || !grad_desc ||
+                  !aligned16(records) || (pos4 && !aligned16(grad_pos))))
         return TP_ERR_INVALID_ARG;
     set_vec_flags(B, desc_vector_ok(cfg, desc), (cfg->desc_dim % 4) == 0 && aligned16(grad_desc));
+    for (int v = 0; v < B.n_views; ++v) B.view[v].pos4 = pos4 ? 1 : 0;
     return from_cuda(tpk::launch_backward(B, W, n, reinterpret_cast<const float4 *>(records), opacity, desc,
                                           cfg->desc_dtype, kept, n_kept, grad_pyramid, grad_pos, grad_size_w,
-                                          grad_opacity, grad_desc, (cudaStream_t)stream));
+                                          grad_opacity, grad_desc, pos, grad_cameras, (cudaStream_t)stream));
 }
 
 template <int MaxV>
@@ -439,6 +446,18 @@ tp_status tp_batch_splat_backward(const tp_config *cfg, const tp_camera *cams, c
                                   grad_pos, grad_size_w, grad_opacity, grad_desc, ws, ws_bytes, stream);
 }
 
+tp_status tp_batch_splat_backward_cameras(const tp_config *cfg, const tp_camera *cams, const int32_t *tiles,
+                                          int32_t n_views, int64_t n, const float *pos, const float *records,
+                                          const float *opacity, const void *desc, const float *grad_pyramid,
+                                          float *grad_pos, float *grad_size_w, float *grad_opacity, float *grad_desc,
+                                          double *grad_cameras, void *ws, int64_t ws_bytes, tp_stream_t stream)
+{
+    if (!grad_cameras) return TP_ERR_INVALID_ARG;
+    return do_backward<kMaxViews>(cfg, cams, tiles, n_views, n, records, opacity, desc, nullptr, nullptr,
+                                  grad_pyramid, grad_pos, grad_size_w, grad_opacity, grad_desc, ws, ws_bytes, stream,
+                                  pos, grad_cameras);
+}
+
 tp_status tp_get_status(const void *ws, tp_stream_t stream, int32_t *device_flags)
 {
     if (!ws || !device_flags) return TP_ERR_INVALID_ARG;
@@ -448,6 +467,7 @@ tp_status tp_get_status(const void *ws, tp_stream_t stream, int32_t *device_flag
     if (e != cudaSuccess) return TP_ERR_CUDA;
     *device_flags = (int32_t)flags;
     if (flags & TP_FLAG_CAPACITY) return TP_ERR_CAPACITY;
+    if (flags & TP_FLAG_BOUNDS) return TP_ERR_BOUNDS;
     if (flags & TP_FLAG_TIMEOUT) return TP_ERR_TIMEOUT;
     if (flags & TP_FLAG_NONFINITE) return TP_ERR_NONFINITE;
     return TP_OK;
@@ -463,6 +483,7 @@ const char *tp_status_string(tp_status status)
     case TP_ERR_TIMEOUT: return "bounded device wait timed out";
     case TP_ERR_CUDA: return "CUDA error";
     case TP_ERR_UNSUPPORTED: return "unsupported configuration";
+    case TP_ERR_BOUNDS: return "out-of-range index caught by the checking build";
     }
     return "unknown status";
 }

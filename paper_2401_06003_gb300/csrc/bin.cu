@@ -61,7 +61,9 @@ __global__ void __launch_bounds__(kBlock) k_project_count(const __grid_constant_
         }
         rec[i] = r;
         const unsigned c = (unsigned)(i & (kCopies - 1));
-        for_each_tile(F, r, [&](int t, int) { atomicAdd(count + (size_t)t * kCopies + c, 1u); });
+        for_each_tile(F, r, [&](int t, int) {
+            if (TP_IN_RANGE(W.status, t >= 0 && t < F.n_tiles)) atomicAdd(count + (size_t)t * kCopies + c, 1u);
+        });
     }
 }
 
@@ -165,6 +167,7 @@ __global__ void __launch_bounds__(kBlock) k_fill(const __grid_constant__ Batch<M
         const float4 pay = make_float4(r.x, r.y, r.w, __ldg(opacity + i));
         const unsigned c = (unsigned)(i & (kCopies - 1));
         for_each_tile(F, r, [&](int t, int L) {
+            if (!TP_IN_RANGE(W.status, t >= 0 && t < F.n_tiles)) return;
             const unsigned long long key = frag_key(r.z, (unsigned)i, L);
             const unsigned e = tile_off[t] + atomicAdd(cursor + (size_t)t * kCopies + c, 1u);
             if (e < W.capacity) {

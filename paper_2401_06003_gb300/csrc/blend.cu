@@ -260,7 +260,7 @@ __device__ int build_topk(const Frame &F, const Workspace &W, int tile, const Ti
     const int TP = F.tile_px, tid = threadIdx.x, NT = blockDim.x;
     const bool owner = tid < TP;
     top.clear();
-    if (prow >= 0) {
+    if (prow >= 0 && TP_IN_RANGE(W.status, prow < W.crows)) {
 #pragma unroll
         for (int m = 0; m < K; ++m) {
             top.key[m] = W.ckey[(long long)m * W.crows + prow];
@@ -284,12 +284,14 @@ __device__ int build_topk(const Frame &F, const Workspace &W, int tile, const Ti
             for (unsigned e = c0 + tid; e < c1; e += NT) {
                 const unsigned long long key = W.bucket_key[e];
                 entry_taps(F, g, W.bucket_pay[e], [&](int px) {
-                    if (key < S.thr[px]) atomicAdd(S.cnt + px, 1u);
+                    if (TP_IN_RANGE(W.status, px >= 0 && px < TP) && key < S.thr[px]) atomicAdd(S.cnt + px, 1u);
                 });
             }
         } else {
             for (unsigned e = c0 + tid; e < c1; e += NT)
-                entry_taps(F, g, W.bucket_pay[e], [&](int px) { atomicAdd(S.cnt + px, 1u); });
+                entry_taps(F, g, W.bucket_pay[e], [&](int px) {
+                    if (TP_IN_RANGE(W.status, px >= 0 && px < TP)) atomicAdd(S.cnt + px, 1u);
+                });
         }
         __syncthreads();
         const unsigned my = S.cnt[tid];
@@ -299,10 +301,13 @@ __device__ int build_topk(const Frame &F, const Workspace &W, int tile, const Ti
             const unsigned long long key = W.bucket_key[e];
             const float4 pay = W.bucket_pay[e];
             entry_taps_w(F, g, pay, [&](int px, float gam) {
+                if (!TP_IN_RANGE(W.status, px >= 0 && px < TP)) return;
                 if (!multi || key < S.thr[px]) {
                     const unsigned q = S.off[px] + atomicAdd(S.cur + px, 1u);
-                    S.ck[q] = key;
-                    S.ce[q] = __float_as_uint(gam);
+                    if (TP_IN_RANGE(W.status, q < 4u * (unsigned)F.chunk)) {
+                        S.ck[q] = key;
+                        S.ce[q] = __float_as_uint(gam);
+                    }
                 }
             });
         }
@@ -410,7 +415,8 @@ __global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_blend(const __grid_consta
     if (!active) nk = 0;
     const int nk_warp = __reduce_max_sync(0xffffffffu, nk);
     const long long pix = B.pix_base[v] + F.pix_base[L] + (long long)k * F.lw[L] + j;
-    if (active) {
+    const bool out_ok = active && TP_IN_RANGE(W.status, pix >= 0 && pix < B.n_pix);
+    if (out_ok) {
         // the largest kept key: the backward's rebuild keeps exactly the keys <= it
         unsigned long long kmax = 0ull;
 #pragma unroll
@@ -421,10 +427,12 @@ __global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_blend(const __grid_consta
         W.kmax[pix] = kmax;
         if (F.coarse && L > 0) {  // the children of the next launch start from this list
             const long long row = coarse_row(B, v, L, j, k);
+            if (TP_IN_RANGE(W.status, row >= 0 && row < W.crows)) {
 #pragma unroll
-            for (int m = 0; m < K; ++m) {
-                W.ckey[(long long)m * W.crows + row] = top.key[m];
-                W.cgam[(long long)m * W.crows + row] = top.e[m];
+                for (int m = 0; m < K; ++m) {
+                    W.ckey[(long long)m * W.crows + row] = top.key[m];
+                    W.cgam[(long long)m * W.crows + row] = top.e[m];
+                }
             }
         }
     }
@@ -447,7 +455,10 @@ __global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_blend(const __grid_consta
     // descriptor rows of the kept points (empty slots: row 0); the keys are dead from here
     unsigned row[K];
 #pragma unroll
-    for (int m = 0; m < K; ++m) row[m] = m < nk ? key_point(top.key[m]) : 0u;
+    for (int m = 0; m < K; ++m) {
+        row[m] = m < nk ? key_point(top.key[m]) : 0u;
+        if (!TP_IN_RANGE(W.status, row[m] < (unsigned long long)W.n_points || m >= nk)) row[m] = 0u;
+    }
     const int D = F.D;
     constexpr int G = DescGroup<DescT>::G;
     for (int d0 = 0; d0 < D; d0 += G) {
@@ -469,7 +480,7 @@ __global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_blend(const __grid_consta
                 }
             }
         }
-        if (active) {
+        if (out_ok) {
             float *out = pyramid + pix * D + d0;
             if (F.desc_vec) {
 #pragma unroll
@@ -480,7 +491,7 @@ __global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_blend(const __grid_consta
             }
         }
     }
-    if (!active) return;
+    if (!out_ok) return;
     if (kept) {
 #pragma unroll
         for (int m = 0; m < K; ++m)
@@ -490,8 +501,8 @@ __global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_blend(const __grid_consta
     if (t_final) t_final[pix] = T;
     if (STATS) {
         // the parent's count, from the previous launch, covers every coarser layer
-        if (parent)
-            nfr += n_frag[B.pix_base[v] + F.pix_base[L + 1] + (long long)(k >> 1) * F.lw[L + 1] + (j >> 1)];
+        const long long ppix = B.pix_base[v] + F.pix_base[L + 1] + (long long)(k >> 1) * F.lw[L + 1] + (j >> 1);
+        if (parent && TP_IN_RANGE(W.status, ppix < B.n_pix)) nfr += n_frag[ppix];
         n_frag[pix] = nfr;
     }
 }
@@ -508,12 +519,23 @@ __device__ __forceinline__ void atomic_add4(float *p, float4 v)
 // point gradients.  G is the pixel's dL/dC; R the running back-to-front term.
 // t0 holds the first channel group of the point's descriptor, loaded by the caller.
 // DC > 0: the descriptor width known at compile time (G stays in registers).
-template <typename DescT, int DC>
+// Camera adjoint of a fragment (Sec. 3.5), accumulated per thread in a
+// shared-memory column cam[q * stride]: dL/d(fx, fy, cx, cy, R[9], t[3]) from
+// the fragment's screen-space gradient (gx, gy, gs), its camera-space one dXc
+// and the point's world position.
+struct CamCol {
+    float *p;        // null: no camera gradient
+    int stride;
+    const float *pos;
+};
+
+template <typename DescT, int DC, bool CAM = false>
 __device__ __forceinline__ void adjoint_fragment(const Frame &F, int L, int j, int k, unsigned i, float x, float y,
                                                  float z, float s, float al, float Tm, const float *G, float &R,
                                                  const DescGroup<DescT> &t0, const DescT *__restrict__ desc,
                                                  float *__restrict__ gpos, float *__restrict__ gsw,
-                                                 float *__restrict__ gop, float *__restrict__ gdesc)
+                                                 float *__restrict__ gop, float *__restrict__ gdesc,
+                                                 const CamCol &cam = CamCol{nullptr, 0, nullptr})
 {
     const int D = DC > 0 ? DC : F.D;
     constexpr int NG = DescGroup<DescT>::G;
@@ -548,10 +570,36 @@ __device__ __forceinline__ void adjoint_fragment(const Frame &F, int L, int j, i
     const float dXc = gx * F.fx * iz;
     const float dYc = gy * F.fy * iz;
     const float dZc = -(gx * (x - F.cx) + gy * (y - F.cy) + gs * s) * iz;
-    atomicAdd(gsw + i, gs * F.fx * iz);
-    atomicAdd(gpos + 3 * (long long)i + 0, F.R[0] * dXc + F.R[3] * dYc + F.R[6] * dZc);
-    atomicAdd(gpos + 3 * (long long)i + 1, F.R[1] * dXc + F.R[4] * dYc + F.R[7] * dZc);
-    atomicAdd(gpos + 3 * (long long)i + 2, F.R[2] * dXc + F.R[5] * dYc + F.R[8] * dZc);
+    const float gX = F.R[0] * dXc + F.R[3] * dYc + F.R[6] * dZc;
+    const float gY = F.R[1] * dXc + F.R[4] * dYc + F.R[7] * dZc;
+    const float gZ = F.R[2] * dXc + F.R[5] * dYc + F.R[8] * dZc;
+    if (F.pos4) {  // packed rows (X, Y, Z, s_w): one vector atomic instead of four scalar ones
+        atomic_add4(gpos + 4 * (long long)i, make_float4(gX, gY, gZ, gs * F.fx * iz));
+    } else {
+        atomicAdd(gsw + i, gs * F.fx * iz);
+        atomicAdd(gpos + 3 * (long long)i + 0, gX);
+        atomicAdd(gpos + 3 * (long long)i + 1, gY);
+        atomicAdd(gpos + 3 * (long long)i + 2, gZ);
+    }
+    if constexpr (CAM) {
+        // x = fx Xc/Zc + cx, y = fy Yc/Zc + cy, s = fx sw/Zc: dx/dfx = (x - cx)/fx, ds/dfx = s/fx
+        float *c = cam.p;
+        const int st = cam.stride;
+        const float ifx = 1.0f / F.fx, ify = 1.0f / F.fy;
+        c[0] += (gx * (x - F.cx) + gs * s) * ifx;
+        c[st] += gy * (y - F.cy) * ify;
+        c[2 * st] += gx;
+        c[3 * st] += gy;
+        const float d[3] = {dXc, dYc, dZc};
+        const float Xw[3] = {__ldg(cam.pos + 3 * (long long)i), __ldg(cam.pos + 3 * (long long)i + 1),
+                             __ldg(cam.pos + 3 * (long long)i + 2)};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+#pragma unroll
+            for (int b = 0; b < 3; ++b) c[(4 + 3 * a + b) * st] += d[a] * Xw[b];  // dL/dR_ab = dL/dXc_a Xw_b
+            c[(13 + a) * st] += d[a];                                             // dL/dt = dL/dXc
+        }
+    }
 }
 
 // Backward with the lists rebuilt from the workspace's tile lists.  The blend
@@ -565,12 +613,16 @@ __device__ __forceinline__ void adjoint_fragment(const Frame &F, int L, int j, i
 // own layer's pixel (each key carries its layer).
 // Registers are capped at 96 for K <= 16 (five 128-thread CTAs per SM); the
 // kept slots are sorted in shared memory, so no register list is live.
-template <int K, typename DescT, int MaxV, int DC>
+// CAM: also the camera gradient of every view, [n_views][16] doubles in gcam
+// (summed over the views' tiles: per-thread shared-memory columns, one
+// reduction and 16 double atomics per CTA).
+template <int K, typename DescT, int MaxV, int DC, bool CAM>
 __global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_backward(const __grid_constant__ Batch<MaxV> B, Workspace W,
                                                           const DescT *__restrict__ desc,
                                 const float *__restrict__ grad_pyr, float *__restrict__ gpos, float *__restrict__ gsw,
                                 float *__restrict__ gop, float *__restrict__ gdesc, long long n,
-                                const float4 *__restrict__ rec_all, const float *__restrict__ opacity)
+                                const float4 *__restrict__ rec_all, const float *__restrict__ opacity,
+                                const float *__restrict__ pos, double *__restrict__ gcam)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (*((volatile unsigned *)W.status) & TP_FLAG_CAPACITY) return;  // the lists were cut short: outputs invalid
@@ -581,8 +633,9 @@ __global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_backward(const __grid_con
     const TileGeom g = tile_geom(F, tile - B.tile_base[v]);
     const int TP = F.tile_px, tid = threadIdx.x, NT = blockDim.x, L = g.L, D = DC > 0 ? DC : F.D;
     const int j = g.x0 + tid % F.tile_w, k = g.y0 + tid / F.tile_w;
-    const bool active = tid < TP && j < F.lw[L] && k < F.lh[L];
     const long long pix = B.pix_base[v] + F.pix_base[L] + (long long)k * F.lw[L] + j;
+    const bool active =
+        tid < TP && j < F.lw[L] && k < F.lh[L] && TP_IN_RANGE(W.status, pix >= 0 && pix < B.n_pix);
     // slot-major private slots in the backward's region: key [K][TP], entry [K][TP], T_m [K][TP]
     unsigned long long *kk = S.ck;
     unsigned *ke = reinterpret_cast<unsigned *>(S.ck + (size_t)K * TP);
@@ -598,6 +651,7 @@ __global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_backward(const __grid_con
     for (unsigned e = beg + tid; e < end; e += NT) {
         const unsigned long long key = W.bucket_key[e];
         entry_taps_w(F, g, W.bucket_pay[e], [&](int px, float gam) {
+            if (!TP_IN_RANGE(W.status, px >= 0 && px < TP)) return;
             if (key <= thr[px]) {
                 const unsigned q = atomicAdd(S.cnt + px, 1u);
                 if (q < (unsigned)K) {
@@ -609,10 +663,16 @@ __global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_backward(const __grid_con
         });
     }
     __syncthreads();
+    float *camc = reinterpret_cast<float *>(S.wsum + 32);  // [16][NT] camera-gradient columns (CAM only)
+    if constexpr (CAM) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) camc[q * NT + tid] = 0.0f;
+    }
+    auto per_pixel = [&]() {
     if (!active) return;
     int nk = (int)S.cnt[tid];
-    if (F.coarse && L + 1 < F.n_layers) {
-        const long long prow = coarse_row(B, v, L + 1, j >> 1, k >> 1);
+    const long long prow = F.coarse && L + 1 < F.n_layers ? coarse_row(B, v, L + 1, j >> 1, k >> 1) : -1ll;
+    if (prow >= 0 && TP_IN_RANGE(W.status, prow < W.crows)) {
         const unsigned long long km = thr[tid];
         for (int m = 0; m < K; ++m) {
             const unsigned long long key = W.ckey[(long long)m * W.crows + prow];
@@ -665,28 +725,44 @@ __global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_backward(const __grid_con
         unsigned long long key[NB];
         float4 pay[NB];
         DescGroup<DescT> t0[NB];
+        unsigned pi[NB];
+        bool ok[NB];
 #pragma unroll
         for (int u = 0; u < NB; ++u) {
             const int m = m1 - u >= 0 ? m1 - u : 0;
             key[u] = kk[m * TP + tid];
+            pi[u] = key_point(key[u]);
             const unsigned ent = ke[m * TP + tid];
+            ok[u] = TP_IN_RANGE(W.status, pi[u] < (unsigned long long)W.n_points &&
+                                              (ent == kNoPoint || ent < W.capacity));
+            if (!ok[u]) pi[u] = 0u;
             if (ent != kNoPoint) {
-                pay[u] = W.bucket_pay[ent];
+                pay[u] = W.bucket_pay[ok[u] ? ent : 0u];
             } else {  // a coarser layer's fragment
-                const unsigned i = key_point(key[u]);
-                const float4 r = rec[i];
-                pay[u] = make_float4(r.x, r.y, r.w, __ldg(opacity + i));
+                const float4 r = rec[pi[u]];
+                pay[u] = make_float4(r.x, r.y, r.w, __ldg(opacity + pi[u]));
             }
-            t0[u] = load_group(desc, key_point(key[u]), D, 0, F.desc_vec);
+            t0[u] = load_group(desc, pi[u], D, 0, F.desc_vec);
         }
 #pragma unroll
         for (int u = 0; u < NB; ++u) {
             const int m = m1 - u;
             if (m < 0) break;
+            if (!ok[u]) continue;
             const int Lf = key_layer(key[u]), d = Lf - L;  // the fragment's own layer and pixel
-            adjoint_fragment<DescT, DC>(F, Lf, j >> d, k >> d, key_point(key[u]), pay[u].x, pay[u].y,
+            adjoint_fragment<DescT, DC, CAM>(F, Lf, j >> d, k >> d, pi[u], pay[u].x, pay[u].y,
                                     __uint_as_float((unsigned)(key[u] >> 32)), pay[u].z, pay[u].w, kt[m * TP + tid],
-                                    G, R, t0[u], desc, gpos, gsw, gop, gdesc);
+                                    G, R, t0[u], desc, gpos, gsw, gop, gdesc, CamCol{camc + tid, NT, pos});
+        }
+    }
+    };
+    per_pixel();
+    if constexpr (CAM) {
+        __syncthreads();
+        if (tid < 16) {
+            float acc = 0.0f;
+            for (int t = 0; t < NT; ++t) acc += camc[tid * NT + t];
+            if (acc != 0.0f) atomicAdd(gcam + 16 * v + tid, (double)acc);
         }
     }
 }
@@ -701,7 +777,8 @@ __global__ void __launch_bounds__(kBlock) k_stored_backward(const __grid_constan
                                                             const unsigned char *__restrict__ n_kept,
                                                             const float *__restrict__ grad_pyr,
                                                             float *__restrict__ gpos, float *__restrict__ gsw,
-                                                            float *__restrict__ gop, float *__restrict__ gdesc)
+                                                            float *__restrict__ gop, float *__restrict__ gdesc,
+                                                            unsigned *status)
 {
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x; pix < B.n_pix; pix += stride) {
@@ -723,6 +800,7 @@ __global__ void __launch_bounds__(kBlock) k_stored_backward(const __grid_constan
             Tm[m] = 0.0f;
             if (m < nk) {
                 const unsigned i = kept[pix * K + m];
+                if (!TP_IN_RANGE(status, (long long)i < n)) continue;
                 const float4 r = rec[i];
                 const FragW w = frag_weights(F, r.x, r.y, r.w, L, j, k);
                 Tm[m] = T;
@@ -737,6 +815,7 @@ __global__ void __launch_bounds__(kBlock) k_stored_backward(const __grid_constan
         for (int m = K - 1; m >= 0; --m) {
             if (m >= nk) continue;
             const unsigned i = kept[pix * K + m];
+            if (!TP_IN_RANGE(status, (long long)i < n)) continue;
             const float4 r = rec[i];
             adjoint_fragment<DescT, 0>(F, L, j, k, i, r.x, r.y, r.z, r.w, __ldg(opacity + i), Tm[m], G, R,
                                     load_group(desc, i, F.D, 0, F.desc_vec), desc, gpos, gsw, gop, gdesc);
@@ -807,46 +886,55 @@ static cudaError_t blend_impl(const Batch<MaxV> &B, const Workspace &W, const vo
     return blend_launches<K, DescT, MaxV, false>(B, W, d, pyramid, kept, n_kept, t_final, n_frag, stream);
 }
 
-template <int K, typename DescT, int MaxV, int DC>
-static cudaError_t backward_launch(const Batch<MaxV> &B, const Workspace &W, const DescT *d, const float *grad_pyr,
-                                   float *gpos, float *gsw, float *gop, float *gdesc, long long n, const float4 *rec,
-                                   const float *opacity, size_t smem, cudaStream_t stream)
+// Point and camera gradients of the recompute backward (BwdArgs bundles the launch's pointers).
+struct BwdArgs {
+    const float *grad_pyr;
+    float *gpos, *gsw, *gop, *gdesc;
+    long long n;
+    const float4 *rec;
+    const float *opacity;
+    const float *pos;  // camera gradients only
+    double *gcam;      // [n_views][16] or null
+};
+
+template <int K, typename DescT, int MaxV, int DC, bool CAM>
+static cudaError_t backward_launch(const Batch<MaxV> &B, const Workspace &W, const DescT *d, const BwdArgs &a,
+                                   size_t smem, cudaStream_t stream)
 {
-    cudaError_t e = prepare_tile_kernel(k_tile_backward<K, DescT, MaxV, DC>, smem, B.max_threads);
+    if (CAM) smem += 16 * sizeof(float) * (size_t)B.max_threads;
+    cudaError_t e = prepare_tile_kernel(k_tile_backward<K, DescT, MaxV, DC, CAM>, smem, B.max_threads);
     if (e != cudaSuccess) return e;
-    k_tile_backward<K, DescT, MaxV, DC><<<B.n_tiles, B.max_threads, smem, stream>>>(B, W, d, grad_pyr, gpos, gsw,
-                                                                                     gop, gdesc, n, rec, opacity);
+    k_tile_backward<K, DescT, MaxV, DC, CAM><<<B.n_tiles, B.max_threads, smem, stream>>>(
+        B, W, d, a.grad_pyr, a.gpos, a.gsw, a.gop, a.gdesc, a.n, a.rec, a.opacity, a.pos, a.gcam);
     return cudaGetLastError();
 }
 
 template <int K, typename DescT, int MaxV>
-static cudaError_t backward_impl(const Batch<MaxV> &B, const Workspace &W, long long n, const float4 *rec,
-                                 const float *opacity, const void *desc, const unsigned *kept,
-                                 const unsigned char *n_kept, const float *grad_pyr, float *gpos, float *gsw,
-                                 float *gop, float *gdesc, cudaStream_t stream)
+static cudaError_t backward_impl(const Batch<MaxV> &B, const Workspace &W, const void *desc, const unsigned *kept,
+                                 const unsigned char *n_kept, const BwdArgs &a, cudaStream_t stream)
 {
     const DescT *d = static_cast<const DescT *>(desc);
     if (kept) {
+        if (a.gcam) return cudaErrorInvalidValue;  // camera gradients come with the recompute backward only
         long long blocks = (B.n_pix + kBlock - 1) / kBlock;
         if (blocks > 152 * 32) blocks = 152 * 32;
         if (blocks < 1) blocks = 1;
-        k_stored_backward<K, DescT, MaxV><<<(int)blocks, kBlock, 0, stream>>>(B, n, rec, opacity, d, kept, n_kept,
-                                                                              grad_pyr, gpos, gsw, gop, gdesc);
+        k_stored_backward<K, DescT, MaxV><<<(int)blocks, kBlock, 0, stream>>>(
+            B, a.n, a.rec, a.opacity, d, kept, n_kept, a.grad_pyr, a.gpos, a.gsw, a.gop, a.gdesc, W.status);
         return cudaGetLastError();
     }
     const size_t smem = backward_region_bytes((size_t)B.max_threads, K) + (3 * (size_t)B.max_threads + 32) * 4;
+    if (a.gcam) {  // batches only: one generic instantiation per K and descriptor type
+        if constexpr (MaxV > 1) return backward_launch<K, DescT, MaxV, 0, true>(B, W, d, a, smem, stream);
+        return cudaErrorInvalidValue;
+    }
     // the common descriptor widths get compile-time instantiations (K = 16)
     if constexpr (K == 16) {
         const int D = B.view[0].D;
-        if (D == 4)
-            return backward_launch<K, DescT, MaxV, 4>(B, W, d, grad_pyr, gpos, gsw, gop, gdesc, n, rec, opacity, smem,
-                                                      stream);
-        if (D == 16)
-            return backward_launch<K, DescT, MaxV, 16>(B, W, d, grad_pyr, gpos, gsw, gop, gdesc, n, rec, opacity,
-                                                       smem, stream);
+        if (D == 4) return backward_launch<K, DescT, MaxV, 4, false>(B, W, d, a, smem, stream);
+        if (D == 16) return backward_launch<K, DescT, MaxV, 16, false>(B, W, d, a, smem, stream);
     }
-    return backward_launch<K, DescT, MaxV, 0>(B, W, d, grad_pyr, gpos, gsw, gop, gdesc, n, rec, opacity, smem,
-                                              stream);
+    return backward_launch<K, DescT, MaxV, 0, false>(B, W, d, a, smem, stream);
 }
 
 #define TPK_DISPATCH_K(KVAL, ...)                                   \
@@ -878,24 +966,27 @@ template <int MaxV>
 cudaError_t launch_backward(const Batch<MaxV> &B, const Workspace &W, long long n, const float4 *rec,
                             const float *opacity, const void *desc, int desc_dtype, const unsigned *kept,
                             const unsigned char *n_kept, const float *grad_pyramid, float *grad_pos,
-                            float *grad_sw, float *grad_opacity, float *grad_desc, cudaStream_t stream)
+                            float *grad_sw, float *grad_opacity, float *grad_desc, const float *pos,
+                            double *grad_cameras, cudaStream_t stream)
 {
     cudaError_t e;
+    if (grad_cameras &&
+        (e = cudaMemsetAsync(grad_cameras, 0, sizeof(double) * 16 * (size_t)B.n_views, stream)) != cudaSuccess)
+        return e;
     if (n == 0) return cudaSuccess;
     const int K = B.view[0].K, D = B.view[0].D;
-    if ((e = cudaMemsetAsync(grad_pos, 0, sizeof(float) * 3 * (size_t)n, stream)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(grad_sw, 0, sizeof(float) * (size_t)n, stream)) != cudaSuccess) return e;
+    const bool pos4 = B.view[0].pos4 != 0;
+    if ((e = cudaMemsetAsync(grad_pos, 0, sizeof(float) * (pos4 ? 4 : 3) * (size_t)n, stream)) != cudaSuccess)
+        return e;
+    if (!pos4 && (e = cudaMemsetAsync(grad_sw, 0, sizeof(float) * (size_t)n, stream)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(grad_opacity, 0, sizeof(float) * (size_t)n, stream)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(grad_desc, 0, sizeof(float) * (size_t)D * (size_t)n, stream)) != cudaSuccess)
         return e;
+    const BwdArgs a{grad_pyramid, grad_pos, grad_sw, grad_opacity, grad_desc, n, rec, opacity, pos, grad_cameras};
     if (desc_dtype == TP_BF16) {
-        TPK_DISPATCH_K(K, return (backward_impl<KC, __nv_bfloat16, MaxV>(B, W, n, rec, opacity, desc, kept, n_kept,
-                                                                        grad_pyramid, grad_pos, grad_sw,
-                                                                        grad_opacity, grad_desc, stream)));
+        TPK_DISPATCH_K(K, return (backward_impl<KC, __nv_bfloat16, MaxV>(B, W, desc, kept, n_kept, a, stream)));
     } else {
-        TPK_DISPATCH_K(K, return (backward_impl<KC, float, MaxV>(B, W, n, rec, opacity, desc, kept, n_kept,
-                                                                grad_pyramid, grad_pos, grad_sw, grad_opacity,
-                                                                grad_desc, stream)));
+        TPK_DISPATCH_K(K, return (backward_impl<KC, float, MaxV>(B, W, desc, kept, n_kept, a, stream)));
     }
     return cudaErrorInvalidValue;
 }
@@ -907,10 +998,11 @@ template cudaError_t launch_blend<kMaxViews>(const Batch<kMaxViews> &, const Wor
                                              cudaStream_t);
 template cudaError_t launch_backward<1>(const Batch<1> &, const Workspace &, long long, const float4 *,
                                         const float *, const void *, int, const unsigned *, const unsigned char *,
-                                        const float *, float *, float *, float *, float *, cudaStream_t);
+                                        const float *, float *, float *, float *, float *, const float *, double *,
+                                        cudaStream_t);
 template cudaError_t launch_backward<kMaxViews>(const Batch<kMaxViews> &, const Workspace &, long long,
                                                 const float4 *, const float *, const void *, int,
                                                 const unsigned *, const unsigned char *, const float *, float *,
-                                                float *, float *, float *, cudaStream_t);
+                                                float *, float *, float *, const float *, double *, cudaStream_t);
 
 }  // namespace tpk

@@ -26,10 +26,13 @@ struct CamArgs {
 constexpr int kCamBlock = 256;
 constexpr int kCamOut = 16;  // fx, fy, cx, cy, R[9], t[3]
 
+// gpos rows are ps floats apart (3, or 4 for packed rows whose fourth float
+// is dL/ds_w); gsw entries are ss floats apart.
 __global__ void __launch_bounds__(kCamBlock) k_camera_grad(CamArgs A, long long n, const float *__restrict__ pos,
                                                            const float4 *__restrict__ rec,
                                                            const float *__restrict__ gpos,
-                                                           const float *__restrict__ gsw, double *__restrict__ out)
+                                                           const float *__restrict__ gsw, int ps, int ss,
+                                                           double *__restrict__ out)
 {
     float acc[kCamOut];
 #pragma unroll
@@ -39,12 +42,12 @@ __global__ void __launch_bounds__(kCamBlock) k_camera_grad(CamArgs A, long long 
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const float4 r = rec[i];
         if (!(r.z > 0.0f)) continue;  // culled: the record is all zero
-        const float g0 = gpos[3 * i], g1 = gpos[3 * i + 1], g2 = gpos[3 * i + 2];
+        const float g0 = gpos[ps * i], g1 = gpos[ps * i + 1], g2 = gpos[ps * i + 2];
         float dXc[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a) dXc[a] = A.M[3 * a] * g0 + A.M[3 * a + 1] * g1 + A.M[3 * a + 2] * g2;
         const float Z = r.z;
-        const float Gx = dXc[0] * Z * A.ifx, Gy = dXc[1] * Z * A.ify, Gs = gsw[i] * Z * A.ifx;
+        const float Gx = dXc[0] * Z * A.ifx, Gy = dXc[1] * Z * A.ify, Gs = gsw[ss * i] * Z * A.ifx;
         acc[0] += (Gx * (r.x - A.cx) + Gs * r.w) * A.ifx;
         acc[1] += Gy * (r.y - A.cy) * A.ify;
         acc[2] += Gx;
@@ -84,8 +87,8 @@ tp_status tp_camera_backward(const tp_camera *cam, int64_t n, const float *pos, 
                              const float *grad_pos, const float *grad_size_w, double *grad_camera, tp_stream_t stream)
 {
     if (!cam || !grad_camera || n < 0) return TP_ERR_INVALID_ARG;
-    if (n > 0 && (!pos || !records || !grad_pos || !grad_size_w || ((uintptr_t)records & 15u) != 0))
-        return TP_ERR_INVALID_ARG;
+    if (n > 0 && (!pos || !records || !grad_pos || ((uintptr_t)records & 15u) != 0)) return TP_ERR_INVALID_ARG;
+    const bool pos4 = grad_size_w == nullptr;  // packed [n][4] rows (X, Y, Z, s_w)
     if (!(cam->fx != 0.0f) || !(cam->fy != 0.0f)) return TP_ERR_INVALID_ARG;
     // (R^T)^-1 = (R^-1)^T: the transposed cofactor matrix of R^T over det R
     const float *R = cam->R;
@@ -116,7 +119,8 @@ tp_status tp_camera_backward(const tp_camera *cam, int64_t n, const float *pos, 
     long long blocks = (n + tpk::kCamBlock - 1) / tpk::kCamBlock;
     if (blocks > 152 * 16) blocks = 152 * 16;
     tpk::k_camera_grad<<<(int)blocks, tpk::kCamBlock, 0, s>>>(A, n, pos, reinterpret_cast<const float4 *>(records),
-                                                              grad_pos, grad_size_w, grad_camera);
+                                                              grad_pos, pos4 ? grad_pos + 3 : grad_size_w,
+                                                              pos4 ? 4 : 3, pos4 ? 4 : 1, grad_camera);
     return cudaGetLastError() == cudaSuccess ? TP_OK : TP_ERR_CUDA;
 }
 

@@ -36,6 +36,7 @@ struct Frame {
     int chunk;             // tile-list entries merged per chunk by the tile kernels
     int desc_vec;          // 1 if descriptors can be read 4 channels at a time
     int grad_vec;          // 1 if descriptor gradients can take 4-channel vector atomics
+    int pos4;              // 1: position gradients are [n][4] rows (X, Y, Z, s_w), one vector atomic each
     int coarse;            // 1: coarse-layer inclusion (a pixel's list also holds the fragments of
                            //    the coarser-layer pixels that contain it, Sec. 3.6)
     int lw[kMaxLayers], lh[kMaxLayers];            // layer sizes W_L, H_L
@@ -125,6 +126,7 @@ struct Workspace {
     unsigned long long *ckey;
     unsigned *cgam;
     long long crows;
+    long long n_points;     // points of the frame (index checks of the checking build)
     unsigned capacity;
 };
 
@@ -300,6 +302,21 @@ __device__ __forceinline__ void raise_flag(unsigned *status, unsigned bit)
     if ((*((volatile unsigned *)status) & bit) == 0u) atomicOr(status, bit);
 }
 
+// Index checks of the checking build (TP_DEBUG): TP_IN_RANGE(status, cond)
+// is cond, and a false cond also sets TP_FLAG_BOUNDS; the caller then skips
+// the access.  In the release build the macro is the constant true and
+// compiles away.
+#ifdef TP_DEBUG
+__device__ __forceinline__ bool in_range_checked(unsigned *status, bool ok)
+{
+    if (!ok) raise_flag(status, TP_FLAG_BOUNDS);
+    return ok;
+}
+#define TP_IN_RANGE(status, cond) ::tpk::in_range_checked((status), (cond))
+#else
+#define TP_IN_RANGE(status, cond) true
+#endif
+
 template <typename T>
 __device__ __forceinline__ float load_desc(const T *p);
 template <>
@@ -327,7 +344,8 @@ template <int MaxV>
 cudaError_t launch_backward(const Batch<MaxV> &B, const Workspace &W, long long n, const float4 *rec,
                             const float *opacity, const void *desc, int desc_dtype, const unsigned *kept,
                             const unsigned char *n_kept, const float *grad_pyramid, float *grad_pos,
-                            float *grad_sw, float *grad_opacity, float *grad_desc, cudaStream_t stream);
+                            float *grad_sw, float *grad_opacity, float *grad_desc, const float *pos,
+                            double *grad_cameras, cudaStream_t stream);
 size_t tile_smem_bytes(const Frame &F, bool backward);
 
 }  // namespace tpk

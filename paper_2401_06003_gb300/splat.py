@@ -31,6 +31,34 @@ def _need(t, dtype, shape, name, device):
                          f"got {t.dtype} {tuple(t.shape)} on {t.device}")
 
 
+def _grad_buffers(n, D, dev, grads):
+    """Point-gradient buffers of a backward call: (pointers for the C call,
+    tensors returned to the caller).  By default the position and size
+    gradients share packed [n, 4] rows (one 16-byte atomic per fragment); the
+    caller gets [n, 3] and [n] views of them.  ``grads`` may hold caller
+    buffers: (pos [n, 3], size_w [n], opacity, desc), or (pos [n, 4] packed,
+    None, opacity, desc)."""
+    if grads is None:
+        g4 = torch.empty((n, 4), dtype=torch.float32, device=dev)
+        grads = (g4, None, torch.empty((n,), dtype=torch.float32, device=dev),
+                 torch.empty((n, D), dtype=torch.float32, device=dev))
+    gp, gs, go, gd = grads
+    if tuple(gp.shape) == (n, 4):
+        return (gp, None, go, gd), (gp[:, :3], gp[:, 3], go, gd)
+    return (gp, gs, go, gd), (gp, gs, go, gd)
+
+
+def _packed_pos_size(grad_pos, grad_size_w):
+    """The packed [n, 4] base of (grad_pos, grad_size_w) views, or None."""
+    n = grad_pos.shape[0]
+    if tuple(grad_pos.shape) == (n, 4) and grad_pos.is_contiguous():
+        return grad_pos
+    if (grad_size_w is not None and grad_pos.stride() == (4, 1) and grad_size_w.stride() == (4,)
+            and grad_size_w.data_ptr() == grad_pos.data_ptr() + 12):
+        return torch.as_strided(grad_pos, (n, 4), (4, 1))
+    return None
+
+
 @dataclasses.dataclass
 class Frame:
     """Outputs of one forward render and what the backward pass needs."""
@@ -137,17 +165,12 @@ class Renderer:
         n = records.shape[0]
         dev = self.device
         _need(grad_pyramid, torch.float32, (self.P, self.D), "grad_pyramid", dev)
-        if grads is None:
-            grads = (torch.empty((n, 3), dtype=torch.float32, device=dev),
-                     torch.empty((n,), dtype=torch.float32, device=dev),
-                     torch.empty((n,), dtype=torch.float32, device=dev),
-                     torch.empty((n, self.D), dtype=torch.float32, device=dev))
-        gp, gs, go, gd = grads
+        (gp, gs, go, gd), out = _grad_buffers(n, self.D, dev, grads)
         st = self.lib.tp_splat_backward(ctypes.byref(self.cfg), ctypes.byref(self.cam), n, _ptr(records),
                                         _ptr(opacity), _ptr(desc), _ptr(kept), _ptr(n_kept), _ptr(grad_pyramid),
                                         _ptr(gp), _ptr(gs), _ptr(go), _ptr(gd), _ptr(ws), ws.numel(), _stream(dev))
         _lib.check("tp_splat_backward", st)
-        return grads
+        return out
 
     def camera_backward(self, pos, records, grad_pos, grad_size_w, out=None) -> torch.Tensor:
         """dL/d(fx, fy, cx, cy, R[0..8], t[0..2]) [16] float64, from this view's point gradients."""
@@ -155,12 +178,15 @@ class Renderer:
         dev = self.device
         _need(pos, torch.float32, (n, 3), "pos", dev)
         _need(records, torch.float32, (n, 4), "records", dev)
-        _need(grad_pos, torch.float32, (n, 3), "grad_pos", dev)
-        _need(grad_size_w, torch.float32, (n,), "grad_size_w", dev)
+        packed = _packed_pos_size(grad_pos, grad_size_w)
+        if packed is None:
+            _need(grad_pos, torch.float32, (n, 3), "grad_pos", dev)
+            _need(grad_size_w, torch.float32, (n,), "grad_size_w", dev)
         if out is None:
             out = torch.empty(16, dtype=torch.float64, device=dev)
-        st = self.lib.tp_camera_backward(ctypes.byref(self.cam), n, _ptr(pos), _ptr(records), _ptr(grad_pos),
-                                         _ptr(grad_size_w), _ptr(out), _stream(dev))
+        st = self.lib.tp_camera_backward(ctypes.byref(self.cam), n, _ptr(pos), _ptr(records),
+                                         _ptr(grad_pos if packed is None else packed),
+                                         _ptr(grad_size_w if packed is None else None), _ptr(out), _stream(dev))
         _lib.check("tp_camera_backward", st)
         return out
 
@@ -341,17 +367,29 @@ class BatchRenderer:
         n = records.shape[1]
         dev = self.device
         _need(grad_pyramid, torch.float32, (self.P, self.D), "grad_pyramid", dev)
-        if grads is None:
-            grads = (torch.empty((n, 3), dtype=torch.float32, device=dev),
-                     torch.empty((n,), dtype=torch.float32, device=dev),
-                     torch.empty((n,), dtype=torch.float32, device=dev),
-                     torch.empty((n, self.D), dtype=torch.float32, device=dev))
-        gp, gs, go, gd = grads
+        (gp, gs, go, gd), out = _grad_buffers(n, self.D, dev, grads)
         st = self.lib.tp_batch_splat_backward(*self._common(), n, _ptr(records), _ptr(opacity), _ptr(desc),
                                               _ptr(kept), _ptr(n_kept), _ptr(grad_pyramid), _ptr(gp), _ptr(gs),
                                               _ptr(go), _ptr(gd), _ptr(ws), ws.numel(), _stream(dev))
         _lib.check("tp_batch_splat_backward", st)
-        return grads
+        return out
+
+    def splat_backward_cameras(self, pos, records, opacity, desc, grad_pyramid, ws, grads=None, grad_cameras=None):
+        """Point gradients (recomputed lists) and every view's camera gradient
+        dL/d(fx, fy, cx, cy, R[0..8], t[0..2]) [n_views, 16] float64 from one pass."""
+        n = records.shape[1]
+        dev = self.device
+        _need(pos, torch.float32, (n, 3), "pos", dev)
+        _need(grad_pyramid, torch.float32, (self.P, self.D), "grad_pyramid", dev)
+        (gp, gs, go, gd), out = _grad_buffers(n, self.D, dev, grads)
+        if grad_cameras is None:
+            grad_cameras = torch.empty((self.n_views, 16), dtype=torch.float64, device=dev)
+        st = self.lib.tp_batch_splat_backward_cameras(*self._common(), n, _ptr(pos), _ptr(records), _ptr(opacity),
+                                                      _ptr(desc), _ptr(grad_pyramid), _ptr(gp), _ptr(gs), _ptr(go),
+                                                      _ptr(gd), _ptr(grad_cameras), _ptr(ws), ws.numel(),
+                                                      _stream(dev))
+        _lib.check("tp_batch_splat_backward_cameras", st)
+        return out, grad_cameras
 
     def status(self, ws) -> int:
         flags = ctypes.c_int32(0)
@@ -408,7 +446,7 @@ def autotune_tiles(cameras, n_layers, pos, size_w, opacity, desc, K=16, candidat
             G = torch.ones((r.P, D), dtype=torch.float32, device=r.device)
             rec = torch.empty((n, 4), dtype=torch.float32, device=r.device)
             pyr = torch.empty((r.P, D), dtype=torch.float32, device=r.device)
-            grads = (torch.empty((n, 3), device=r.device), torch.empty((n,), device=r.device),
+            grads = (torch.empty((n, 4), device=r.device), None,  # packed position/size rows
                      torch.empty((n,), device=r.device), torch.empty((n, D), device=r.device))
             ms = []
             try:
@@ -472,7 +510,7 @@ def autotune_batch_tiles(cameras, n_layers, pos, size_w, opacity, desc, K=16, ca
         G = torch.ones((br.P, D), dtype=torch.float32, device=br.device)
         rec = torch.empty((V, n, 4), dtype=torch.float32, device=br.device)
         pyr = torch.empty((br.P, D), dtype=torch.float32, device=br.device)
-        grads = (torch.empty((n, 3), device=br.device), torch.empty((n,), device=br.device),
+        grads = (torch.empty((n, 4), device=br.device), None,  # packed position/size rows
                  torch.empty((n,), device=br.device), torch.empty((n, D), device=br.device))
         ms = []
         try:

@@ -29,6 +29,14 @@ def test_exports_every_declared_symbol(lib):
     assert lib.tp_version() >= 100
 
 
+def test_checking_build_exports_every_declared_symbol():
+    """libtrips_debug.so (TP_DEBUG index checks) is the same ABI."""
+    dbg = _lib.load(build(debug=True))
+    for name in _lib.header_functions():
+        assert hasattr(dbg, name), name
+    assert dbg.tp_status_string(_lib.TP_ERR_BOUNDS).decode().startswith("out-of-range")
+
+
 def test_struct_layout_matches_header():
     assert ctypes.sizeof(_lib.tp_camera) == 17 * 4 + 2 * 4
     assert ctypes.sizeof(_lib.tp_config) == 9 * 4

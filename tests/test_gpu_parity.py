@@ -359,3 +359,27 @@ def _error_stats(got, ref):
     return {"max_abs": float(e.max()), "mean_abs": float(e.mean()), "max_ref": scale,
             "max_rel": float(rel.max()), "mean_rel": float(rel.mean()),
             "frac_rel_above_1e-2": float((rel > 1e-2).mean())}
+
+
+def test_packed_and_separate_gradient_layouts_agree(cube):
+    """grad_size_w NULL selects packed [n][4] (X, Y, Z, s_w) rows; the separate
+    [n][3] + [n] layout gives the same gradients (both modes, and the camera
+    adjoint reads either)."""
+    n, D = cube.n, cube.D
+    for mode in ("store", "recompute"):
+        r, fr, ins, _ = gpu_frame(cube, mode=mode)
+        G = to_dev(np.random.default_rng(26).uniform(-1, 1, (r.P, D)).astype(np.float32))
+        lists = (fr.kept, fr.n_kept) if mode == "store" else (None, None)
+        packed = r.splat_backward(fr.records, ins[2], ins[3], G, fr.workspace, *lists)
+        assert packed[0].stride() == (4, 1) and packed[1].stride() == (4,)
+        sep = (torch.empty((n, 3), device=device()), torch.empty((n,), device=device()),
+               torch.empty((n,), device=device()), torch.empty((n, D), device=device()))
+        separate = r.splat_backward(fr.records, ins[2], ins[3], G, fr.workspace, *lists, grads=sep)
+        assert separate[0].is_contiguous()
+        for a, b, name in zip(packed, separate, ("pos", "size_w", "opacity", "desc")):
+            assert_close_scaled(a.cpu().numpy().reshape(n, -1), b.cpu().numpy().reshape(n, -1), 1e-4,
+                                name=f"{mode} packed vs separate grad_{name}")
+        ca = r.camera_backward(ins[0], fr.records, packed[0], packed[1]).cpu().numpy()
+        cb = r.camera_backward(ins[0], fr.records, separate[0], separate[1]).cpu().numpy()
+        assert_close_scaled(ca, cb, 1e-4, name=f"{mode} camera gradient from packed rows",
+                            segments=[(0, 4), (4, 13), (13, 16)])
