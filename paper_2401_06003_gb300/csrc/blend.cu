@@ -221,6 +221,37 @@ struct TopK {
         n = n < K ? n + 1 : K;
     }
 
+    // The chain over slots [0, L) only: exact while n < L, since slots from n
+    // on are empty and the chain only moves empty keys past slot n.
+    template <int L>
+    __device__ __forceinline__ void insert_first(unsigned long long k, unsigned ee)
+    {
+#pragma unroll
+        for (int m = 0; m < L; ++m) {
+            const bool lt = k < key[m];
+            const unsigned long long tk = key[m];
+            const unsigned te = e[m];
+            key[m] = lt ? k : tk;
+            e[m] = lt ? ee : te;
+            k = lt ? tk : k;
+            ee = lt ? te : ee;
+        }
+        n = n < K ? n + 1 : K;
+    }
+
+    // Insertion with a chain of lim slots rounded up to a multiple of K/4;
+    // lim is the same for the whole warp (one uniform branch, no divergence)
+    // and above every lane's n.  Most pixels hold far fewer than K
+    // candidates, so their warps run short chains.
+    __device__ __forceinline__ void insert_bounded(unsigned long long k, unsigned ee, int lim)
+    {
+        if (k >= key[K - 1]) return;
+        if (lim <= K / 4) insert_first<K / 4>(k, ee);
+        else if (lim <= K / 2) insert_first<K / 2>(k, ee);
+        else if (lim <= 3 * K / 4) insert_first<3 * K / 4>(k, ee);
+        else insert_first<K>(k, ee);
+    }
+
     // The same chain stopped at slot n: slots past the n valid ones are empty.
     // Cheaper when lists are short (sorting the backward's kept slots).
     __device__ __forceinline__ void insert_short(unsigned long long k, unsigned ee)
@@ -312,9 +343,12 @@ __device__ int build_topk(const Frame &F, const Workspace &W, int tile, const Ti
             });
         }
         __syncthreads();
+        // every list of the warp stays below lim slots during this chunk's merge
+        const int lim = min(K, __reduce_max_sync(0xffffffffu, owner ? top.n : 0) +
+                                   (int)__reduce_max_sync(0xffffffffu, owner ? my : 0u));
         if (owner) {
             const unsigned a = S.off[tid];
-            for (unsigned q = a; q < a + my; ++q) top.insert(S.ck[q], S.ce[q]);
+            for (unsigned q = a; q < a + my; ++q) top.insert_bounded(S.ck[q], S.ce[q], lim);
             if (multi) S.thr[tid] = top.key[K - 1];
             nfr += my;
         }
