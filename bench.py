@@ -318,7 +318,7 @@ def run_ours(args):
         r.splat_forward(rec, op, ws)
         if ev is not None:
             ev[2].record(stream)
-        _, kept, nk, _, _ = r.blend(N, desc, ws, store_lists=store, pyramid=pyr)
+        _, kept, nk, _, _ = r.blend(rec, op, desc, ws, store_lists=store, pyramid=pyr)
         if ev is not None:
             ev[3].record(stream)
         r.splat_backward(rec, op, desc, G, ws, kept if store else None, nk if store else None, grads=grads)
@@ -356,7 +356,7 @@ def run_ours(args):
                 for q, name in enumerate(["project", "splat", "blend", "backward"])}
 
     # counters of the frame (untimed)
-    _, kept, nk, tfin, nfrag = r.blend(N, desc, ws, stats=True)
+    _, kept, nk, tfin, nfrag = r.blend(rec, op, desc, ws, stats=True)
     V = int((rec[:, 2] > 0).sum().item())
     F = int(nfrag.to(torch.int64).sum().item())
     Fk = int(nk.to(torch.int64).sum().item())
@@ -415,7 +415,7 @@ def run_ours(args):
                 pb, swb, opb, db = d_in[b]
                 r.project(pb, swb, ws, records=rec)
                 r.splat_forward(rec, opb, ws)
-                _, kept_b, nk_b, _, _ = r.blend(N, db, ws, store_lists=store, pyramid=pyr)
+                _, kept_b, nk_b, _, _ = r.blend(rec, opb, db, ws, store_lists=store, pyramid=pyr)
                 r.splat_backward(rec, opb, db, G, ws, kept_b if store else None, nk_b if store else None,
                                  grads=tuple(d_gr[b]))
                 computed[b].record(stream)
@@ -450,7 +450,7 @@ def run_ours(args):
     for _ in range(args.steps):
         r.project(pos, sw, ws, records=rec)
         r.splat_forward(rec, op, ws)
-        r.blend(N, desc, ws, pyramid=pyr)
+        r.blend(rec, op, desc, ws, pyramid=pyr)
     f1.record(stream)
     torch.cuda.synchronize(dev)
     fwd_ms = max_over_ranks(f0.elapsed_time(f1), world, dev) / args.steps
@@ -466,7 +466,7 @@ def run_ours(args):
         def step32():
             rf.project(pos, sw, ws, records=rec)
             rf.splat_forward(rec, op, ws)
-            _, k32, n32, _, _ = rf.blend(N, desc32, ws, store_lists=store, pyramid=pyr)
+            _, k32, n32, _, _ = rf.blend(rec, op, desc32, ws, store_lists=store, pyramid=pyr)
             rf.splat_backward(rec, op, desc32, G, ws, k32 if store else None, n32 if store else None, grads=grads)
 
         for _ in range(args.warmup):
@@ -493,7 +493,7 @@ def run_ours(args):
         def step_c():
             rc.project(pos, sw, ws_c, records=rec)
             rc.splat_forward(rec, op, ws_c)
-            rc.blend(N, desc, ws_c, pyramid=pyr)
+            rc.blend(rec, op, desc, ws_c, pyramid=pyr)
             rc.splat_backward(rec, op, desc, G, ws_c, grads=grads)
 
         def timed(fn):
@@ -510,7 +510,7 @@ def run_ours(args):
 
         ms_c = timed(step_c)
         fwd_c = timed(lambda: (rc.project(pos, sw, ws_c, records=rec), rc.splat_forward(rec, op, ws_c),
-                               rc.blend(N, desc, ws_c, pyramid=pyr)))
+                               rc.blend(rec, op, desc, ws_c, pyramid=pyr)))
         inclusion = {"ms_per_step": round(ms_c, 4), "overhead_ms": round(ms_c - ms_per_step, 4),
                      "forward_ms": round(fwd_c, 4), "forward_overhead_ms": round(fwd_c - fwd_ms, 4),
                      "flags": rc.status(ws_c), "workspace_bytes": int(ws_c.numel())}
@@ -652,7 +652,7 @@ def run_batch(args):
     def step():
         br.project(pos, sw, ws, records=rec)
         br.splat_forward(rec, op, ws)
-        br.blend(N, desc, ws, pyramid=pyr)
+        br.blend(rec, op, desc, ws, pyramid=pyr)
         br.splat_backward(rec, op, desc, G, ws, grads=grads)
 
     side = torch.cuda.Stream(dev)
@@ -708,7 +708,7 @@ def run_batch(args):
             e0.record(stream)
             r.project(pos, sw, wsv, records=recv)
             r.splat_forward(recv, op, wsv)
-            r.blend(N, desc, wsv, pyramid=pyrv)
+            r.blend(recv, op, desc, wsv, pyramid=pyrv)
             r.splat_backward(recv, op, desc, Gv, wsv, grads=grads)
             e1.record(stream)
             torch.cuda.synchronize(dev)

@@ -214,18 +214,21 @@ TP_API tp_status tp_splat_forward(const tp_config *cfg, const tp_camera *cam, in
  * pixel, the K smallest (z, index) fragments in order, blended front to back:
  *   C = sum_m T_m gamma_m tau_m,  T_m = prod_{i<m} (1 - gamma_i),
  *   gamma = beta iota alpha (Eq. 3).
- * The fragments come from the workspace's tile lists (tp_splat_forward).
+ * The fragments come from the workspace's tile lists (tp_splat_forward);
+ * each kept fragment's opacity gamma is evaluated again from its point's
+ * record and opacity (the same float32 operations as the lists use).
  * The call also leaves each pixel's largest kept key in the workspace, for a
  * TP_RECOMPUTE backward pass.
- *   desc [n][D] (device, read)
+ *   records [n][4] (device, read; from tp_project, 16-byte aligned),
+ *   opacity [n] (device, read), desc [n][D] (device, read)
  *   pyramid [P][D] (device, written; every pixel)
  *   kept [P][K], n_kept [P], t_final [P], n_frag [P] (device, written;
  *   each may be NULL).  kept and n_kept are what tp_splat_backward reads in
  *   TP_STORE_LISTS mode.
  */
-TP_API tp_status tp_blend(const tp_config *cfg, const tp_camera *cam, int64_t n, const void *desc, float *pyramid,
-                          uint32_t *kept, uint8_t *n_kept, float *t_final, uint32_t *n_frag, void *ws,
-                          int64_t ws_bytes, tp_stream_t stream);
+TP_API tp_status tp_blend(const tp_config *cfg, const tp_camera *cam, int64_t n, const float *records,
+                          const float *opacity, const void *desc, float *pyramid, uint32_t *kept, uint8_t *n_kept,
+                          float *t_final, uint32_t *n_frag, void *ws, int64_t ws_bytes, tp_stream_t stream);
 
 /*
  * Backward pass (Sec. 3.6 "for the backwards pass, the sorted per-pixel lists
@@ -387,8 +390,9 @@ TP_API tp_status tp_batch_splat_forward(const tp_config *cfg, const tp_camera *c
                                         void *ws, int64_t ws_bytes, tp_stream_t stream);
 
 TP_API tp_status tp_batch_blend(const tp_config *cfg, const tp_camera *cams, const int32_t *tiles, int32_t n_views,
-                                int64_t n, const void *desc, float *pyramid, uint32_t *kept, uint8_t *n_kept,
-                                float *t_final, uint32_t *n_frag, void *ws, int64_t ws_bytes, tp_stream_t stream);
+                                int64_t n, const float *records, const float *opacity, const void *desc,
+                                float *pyramid, uint32_t *kept, uint8_t *n_kept, float *t_final, uint32_t *n_frag,
+                                void *ws, int64_t ws_bytes, tp_stream_t stream);
 
 TP_API tp_status tp_batch_splat_backward(const tp_config *cfg, const tp_camera *cams, const int32_t *tiles,
                                          int32_t n_views, int64_t n, const float *records, const float *opacity,

@@ -55,7 +55,7 @@ _SIGS = {
     "tp_splat_forward": (ctypes.c_int, [ctypes.POINTER(tp_config), ctypes.POINTER(tp_camera), _I64, _P, _P, _P,
                                         _I64, _P]),
     "tp_blend": (ctypes.c_int, [ctypes.POINTER(tp_config), ctypes.POINTER(tp_camera), _I64, _P, _P, _P, _P, _P, _P,
-                                _P, _I64, _P]),
+                                _P, _P, _P, _I64, _P]),
     "tp_splat_backward": (ctypes.c_int, [ctypes.POINTER(tp_config), ctypes.POINTER(tp_camera), _I64, _P, _P, _P, _P,
                                          _P, _P, _P, _P, _P, _P, _P, _I64, _P]),
     "tp_batch_pixels": (_I64, [_P, ctypes.c_int32, ctypes.c_int32, _P]),
@@ -65,7 +65,7 @@ _SIGS = {
     "tp_batch_splat_forward": (ctypes.c_int, [ctypes.POINTER(tp_config), _P, _P, ctypes.c_int32, _I64, _P, _P, _P,
                                               _I64, _P]),
     "tp_batch_blend": (ctypes.c_int, [ctypes.POINTER(tp_config), _P, _P, ctypes.c_int32, _I64, _P, _P, _P, _P, _P,
-                                      _P, _P, _I64, _P]),
+                                      _P, _P, _P, _P, _I64, _P]),
     "tp_batch_splat_backward": (ctypes.c_int, [ctypes.POINTER(tp_config), _P, _P, ctypes.c_int32, _I64, _P, _P, _P,
                                                _P, _P, _P, _P, _P, _P, _P, _P, _I64, _P]),
     "tp_batch_splat_backward_cameras": (ctypes.c_int, [ctypes.POINTER(tp_config), _P, _P, ctypes.c_int32, _I64,

@@ -97,16 +97,15 @@ tp_status make_frame(const tp_config *cfg, const tp_camera *cam, int tw, int th,
     F.tile_base[F.n_layers] = tiles;
     F.n_tiles = tiles;
     // Tile CTAs: one thread per pixel, kept lists in registers; shared memory
-    // holds one chunk of tile-list entries' fragments (12 bytes each, at most
-    // four per entry: 48 bytes per chunk entry), sized to about 40 KB per CTA,
-    // or 28 KB for wide descriptors, whose gathers gain more from the L1 that
-    // the smaller carve-out leaves (measured: D = 16, 4K frame, -5% blend time;
-    // D = 4, 1080p, +1%).
+    // holds one chunk of tile-list entries' fragment keys (8 bytes each, at
+    // most four per entry: 32 bytes per chunk entry), sized to about 34 KB per
+    // CTA (six 128-thread CTAs per SM), or 28 KB for wide descriptors, whose
+    // gathers gain more from the L1 that the smaller carve-out leaves.
     F.tile_px = tw * th;
     F.tile_threads = (F.tile_px + 31) / 32 * 32;
-    const int64_t budget = (cfg->desc_dim > 8 ? 28 : 40) * 1024;
+    const int64_t budget = (cfg->desc_dim > 8 ? 28 : 34) * 1024;
     const int64_t avail = budget - (3 * F.tile_threads + 32) * 4;
-    int64_t chunk = avail / 48;
+    int64_t chunk = avail / 32;
     if (chunk < 128) chunk = 128;
     if (chunk > 2048) chunk = 2048;
     F.chunk = (int)((chunk + 15) / 16 * 16);
@@ -290,15 +289,17 @@ tp_status do_splat_forward(const tp_config *cfg, const tp_camera *cams, const in
 
 template <int MaxV>
 tp_status do_blend(const tp_config *cfg, const tp_camera *cams, const int32_t *tiles, int n_views, int64_t n,
-                   const void *desc, float *pyramid, uint32_t *kept, uint8_t *n_kept, float *t_final,
-                   uint32_t *n_frag, void *ws, int64_t ws_bytes, tp_stream_t stream)
+                   const float *records, const float *opacity, const void *desc, float *pyramid, uint32_t *kept,
+                   uint8_t *n_kept, float *t_final, uint32_t *n_frag, void *ws, int64_t ws_bytes, tp_stream_t stream)
 {
     Batch<MaxV> B;
     Workspace W;
     tp_status s = batch_checks(cfg, cams, tiles, n_views, n, ws, ws_bytes, B, W);
     if (s != TP_OK) return s;
     if (!pyramid) return TP_ERR_INVALID_ARG;
-    if (n > 0 && !desc) return TP_ERR_INVALID_ARG;
+    if (n > 0 && (!desc || !records || !opacity || !aligned16(records))) return TP_ERR_INVALID_ARG;
+    W.rec = reinterpret_cast<const float4 *>(records);
+    W.opacity = opacity;
     set_vec_flags(B, desc_vector_ok(cfg, desc) && aligned16(pyramid), 0);
     return from_cuda(tpk::launch_blend(B, W, desc, cfg->desc_dtype, pyramid, kept, n_kept, t_final, n_frag,
                                        (cudaStream_t)stream));
@@ -377,11 +378,12 @@ tp_status tp_splat_forward(const tp_config *cfg, const tp_camera *cam, int64_t n
     return do_splat_forward<1>(cfg, cam, nullptr, 1, n, records, opacity, ws, ws_bytes, stream);
 }
 
-tp_status tp_blend(const tp_config *cfg, const tp_camera *cam, int64_t n, const void *desc, float *pyramid,
-                   uint32_t *kept, uint8_t *n_kept, float *t_final, uint32_t *n_frag, void *ws, int64_t ws_bytes,
-                   tp_stream_t stream)
+tp_status tp_blend(const tp_config *cfg, const tp_camera *cam, int64_t n, const float *records, const float *opacity,
+                   const void *desc, float *pyramid, uint32_t *kept, uint8_t *n_kept, float *t_final,
+                   uint32_t *n_frag, void *ws, int64_t ws_bytes, tp_stream_t stream)
 {
-    return do_blend<1>(cfg, cam, nullptr, 1, n, desc, pyramid, kept, n_kept, t_final, n_frag, ws, ws_bytes, stream);
+    return do_blend<1>(cfg, cam, nullptr, 1, n, records, opacity, desc, pyramid, kept, n_kept, t_final, n_frag, ws,
+                       ws_bytes, stream);
 }
 
 tp_status tp_splat_backward(const tp_config *cfg, const tp_camera *cam, int64_t n, const float *records,
@@ -428,11 +430,12 @@ tp_status tp_batch_splat_forward(const tp_config *cfg, const tp_camera *cams, co
 }
 
 tp_status tp_batch_blend(const tp_config *cfg, const tp_camera *cams, const int32_t *tiles, int32_t n_views,
-                         int64_t n, const void *desc, float *pyramid, uint32_t *kept, uint8_t *n_kept,
-                         float *t_final, uint32_t *n_frag, void *ws, int64_t ws_bytes, tp_stream_t stream)
+                         int64_t n, const float *records, const float *opacity, const void *desc, float *pyramid,
+                         uint32_t *kept, uint8_t *n_kept, float *t_final, uint32_t *n_frag, void *ws,
+                         int64_t ws_bytes, tp_stream_t stream)
 {
-    return do_blend<kMaxViews>(cfg, cams, tiles, n_views, n, desc, pyramid, kept, n_kept, t_final, n_frag, ws,
-                               ws_bytes, stream);
+    return do_blend<kMaxViews>(cfg, cams, tiles, n_views, n, records, opacity, desc, pyramid, kept, n_kept, t_final,
+                               n_frag, ws, ws_bytes, stream);
 }
 
 tp_status tp_batch_splat_backward(const tp_config *cfg, const tp_camera *cams, const int32_t *tiles,
@@ -488,6 +491,6 @@ const char *tp_status_string(tp_status status)
     return "unknown status";
 }
 
-int32_t tp_version(void) { return 120; }
+int32_t tp_version(void) { return 130; }
 
 }  // extern "C"

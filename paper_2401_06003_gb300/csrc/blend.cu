@@ -46,12 +46,11 @@ __device__ __forceinline__ TileGeom tile_geom(const Frame &F, int tile)
     return g;
 }
 
-// Shared-memory layout of a tile CTA: the current chunk's fragments grouped
-// by pixel (keys, then 32-bit payloads) and the per-pixel counters.  Every
-// piece starts on a 16-byte boundary whatever the chunk size.
+// Shared-memory layout of a tile CTA: the current chunk's fragment keys
+// grouped by pixel and the per-pixel counters.  Every piece starts on a
+// 16-byte boundary whatever the chunk size.
 struct TileSmem {
     unsigned long long *ck;      // [4 chunk] chunk fragment keys, grouped by pixel
-    unsigned *ce;                // [4 chunk] chunk fragment payloads
     unsigned *cnt, *off, *cur;   // [tile_threads]
     unsigned *wsum;              // [32]
     unsigned long long *thr;     // [blockDim] a pixel's current K-th key (forward only)
@@ -59,12 +58,9 @@ struct TileSmem {
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~(size_t)15; }
 
-// Bytes of the blend's fragment region (one chunk: 8-byte key and 4-byte
-// payload for at most four fragments per entry).
-__host__ __device__ inline size_t tile_region_bytes(const Frame &F)
-{
-    return align16((size_t)32 * F.chunk) + align16((size_t)16 * F.chunk);
-}
+// Bytes of the blend's fragment region (one chunk: an 8-byte key for at most
+// four fragments per entry).
+__host__ __device__ inline size_t tile_region_bytes(const Frame &F) { return align16((size_t)32 * F.chunk); }
 
 // The counters are sized by the launch's block (the largest tile CTA of the
 // batch), which may exceed this view's own tile_threads.
@@ -73,7 +69,6 @@ __device__ __forceinline__ TileSmem carve(const Frame &F, unsigned char *base)
     TileSmem m;
     const size_t NT = blockDim.x;
     m.ck = reinterpret_cast<unsigned long long *>(base);
-    m.ce = reinterpret_cast<unsigned *>(base + align16((size_t)32 * F.chunk));
     m.cnt = reinterpret_cast<unsigned *>(base + tile_region_bytes(F));
     m.off = m.cnt + NT;
     m.cur = m.off + NT;
@@ -91,7 +86,6 @@ __device__ __forceinline__ TileSmem carve_backward(int K, unsigned char *base)
     TileSmem m;
     const size_t NT = blockDim.x;
     m.ck = reinterpret_cast<unsigned long long *>(base);
-    m.ce = nullptr;
     m.cnt = reinterpret_cast<unsigned *>(base + backward_region_bytes(NT, K));
     m.off = m.cnt + NT;
     m.cur = m.off + NT;
@@ -181,60 +175,36 @@ __device__ __forceinline__ void entry_taps_w(const Frame &F, const TileGeom &g, 
     }
 }
 
-// A pixel's kept list: the K smallest keys seen so far in ascending order,
-// each with a 32-bit payload (the forward build keeps the fragment opacity
-// gamma as float bits, the backward the workspace entry); empty slots hold
-// kEmptyKey.
+// A pixel's kept list: the K smallest fragment keys seen so far, ascending;
+// empty slots hold kEmptyKey.  Only the keys travel through the insertion
+// chain (the fragment opacities are evaluated again for the kept ones), so a
+// chain step is two compares and four selects on 32-bit halves.
 template <int K>
 struct TopK {
     static_assert(K % 4 == 0, "K must be a multiple of 4");
     unsigned long long key[K];
-    unsigned e[K];
     int n;  // valid slots
 
     __device__ __forceinline__ void clear()
     {
         n = 0;
 #pragma unroll
-        for (int m = 0; m < K; ++m) {
-            key[m] = kEmptyKey;
-            e[m] = 0u;
-        }
+        for (int m = 0; m < K; ++m) key[m] = kEmptyKey;
     }
 
-    // Compare-exchange chain: after slot m, slots 0..m hold the m+1 smallest
-    // of (old slots 0..m, new key) in order; the largest key falls off the end.
-    // Straight-line code: cheapest when lists are long (the forward build).
-    __device__ __forceinline__ void insert(unsigned long long k, unsigned ee)
-    {
-        if (k >= key[K - 1]) return;
-#pragma unroll
-        for (int m = 0; m < K; ++m) {
-            const bool lt = k < key[m];
-            const unsigned long long tk = key[m];
-            const unsigned te = e[m];
-            key[m] = lt ? k : tk;
-            e[m] = lt ? ee : te;
-            k = lt ? tk : k;
-            ee = lt ? te : ee;
-        }
-        n = n < K ? n + 1 : K;
-    }
-
-    // The chain over slots [0, L) only: exact while n < L, since slots from n
-    // on are empty and the chain only moves empty keys past slot n.
+    // Compare-exchange chain over slots [0, L): after slot m, slots 0..m
+    // hold the m+1 smallest of (old slots 0..m, new key) in order.  Exact
+    // while n < L: slots from n on are empty and the chain only moves empty
+    // keys past slot n.
     template <int L>
-    __device__ __forceinline__ void insert_first(unsigned long long k, unsigned ee)
+    __device__ __forceinline__ void insert_first(unsigned long long k)
     {
 #pragma unroll
         for (int m = 0; m < L; ++m) {
-            const bool lt = k < key[m];
             const unsigned long long tk = key[m];
-            const unsigned te = e[m];
+            const bool lt = k < tk;
             key[m] = lt ? k : tk;
-            e[m] = lt ? ee : te;
             k = lt ? tk : k;
-            ee = lt ? te : ee;
         }
         n = n < K ? n + 1 : K;
     }
@@ -243,32 +213,13 @@ struct TopK {
     // lim is the same for the whole warp (one uniform branch, no divergence)
     // and above every lane's n.  Most pixels hold far fewer than K
     // candidates, so their warps run short chains.
-    __device__ __forceinline__ void insert_bounded(unsigned long long k, unsigned ee, int lim)
+    __device__ __forceinline__ void insert_bounded(unsigned long long k, int lim)
     {
         if (k >= key[K - 1]) return;
-        if (lim <= K / 4) insert_first<K / 4>(k, ee);
-        else if (lim <= K / 2) insert_first<K / 2>(k, ee);
-        else if (lim <= 3 * K / 4) insert_first<3 * K / 4>(k, ee);
-        else insert_first<K>(k, ee);
-    }
-
-    // The same chain stopped at slot n: slots past the n valid ones are empty.
-    // Cheaper when lists are short (sorting the backward's kept slots).
-    __device__ __forceinline__ void insert_short(unsigned long long k, unsigned ee)
-    {
-        if (k >= key[K - 1]) return;
-#pragma unroll
-        for (int m = 0; m < K; ++m) {
-            if (m > n) break;
-            const bool lt = k < key[m];
-            const unsigned long long tk = key[m];
-            const unsigned te = e[m];
-            key[m] = lt ? k : tk;
-            e[m] = lt ? ee : te;
-            k = lt ? tk : k;
-            ee = lt ? te : ee;
-        }
-        n = n < K ? n + 1 : K;
+        if (lim <= K / 4) insert_first<K / 4>(k);
+        else if (lim <= K / 2) insert_first<K / 2>(k);
+        else if (lim <= 3 * K / 4) insert_first<3 * K / 4>(k);
+        else insert_first<K>(k);
     }
 };
 
@@ -295,7 +246,6 @@ __device__ int build_topk(const Frame &F, const Workspace &W, int tile, const Ti
 #pragma unroll
         for (int m = 0; m < K; ++m) {
             top.key[m] = W.ckey[(long long)m * W.crows + prow];
-            top.e[m] = W.cgam[(long long)m * W.crows + prow];
             top.n += top.key[m] != kEmptyKey ? 1 : 0;
         }
     }
@@ -330,15 +280,11 @@ __device__ int build_topk(const Frame &F, const Workspace &W, int tile, const Ti
         __syncthreads();
         for (unsigned e = c0 + tid; e < c1; e += NT) {
             const unsigned long long key = W.bucket_key[e];
-            const float4 pay = W.bucket_pay[e];
-            entry_taps_w(F, g, pay, [&](int px, float gam) {
+            entry_taps(F, g, W.bucket_pay[e], [&](int px) {
                 if (!TP_IN_RANGE(W.status, px >= 0 && px < TP)) return;
                 if (!multi || key < S.thr[px]) {
                     const unsigned q = S.off[px] + atomicAdd(S.cur + px, 1u);
-                    if (TP_IN_RANGE(W.status, q < 4u * (unsigned)F.chunk)) {
-                        S.ck[q] = key;
-                        S.ce[q] = __float_as_uint(gam);
-                    }
+                    if (TP_IN_RANGE(W.status, q < 4u * (unsigned)F.chunk)) S.ck[q] = key;
                 }
             });
         }
@@ -348,7 +294,7 @@ __device__ int build_topk(const Frame &F, const Workspace &W, int tile, const Ti
                                    (int)__reduce_max_sync(0xffffffffu, owner ? my : 0u));
         if (owner) {
             const unsigned a = S.off[tid];
-            for (unsigned q = a; q < a + my; ++q) top.insert_bounded(S.ck[q], S.ce[q], lim);
+            for (unsigned q = a; q < a + my; ++q) top.insert_bounded(S.ck[q], lim);
             if (multi) S.thr[tid] = top.key[K - 1];
             nfr += my;
         }
@@ -424,7 +370,7 @@ __device__ __forceinline__ DescGroup<DescT> load_group(const DescT *__restrict__
 // layer < 0: every tile of the batch; else the tiles of that layer (the
 // coarse-to-fine launches of coarse-layer inclusion).
 template <int K, typename DescT, int MaxV, bool STATS>
-__global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_blend(const __grid_constant__ Batch<MaxV> B, Workspace W,
+__global__ void __maxnreg__(K <= 16 ? 80 : 168) k_tile_blend(const __grid_constant__ Batch<MaxV> B, Workspace W,
                                              const DescT *__restrict__ desc,
                              float *__restrict__ pyramid, unsigned *__restrict__ kept,
                              unsigned char *__restrict__ n_kept, float *__restrict__ t_final,
@@ -463,36 +409,67 @@ __global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_blend(const __grid_consta
             const long long row = coarse_row(B, v, L, j, k);
             if (TP_IN_RANGE(W.status, row >= 0 && row < W.crows)) {
 #pragma unroll
-                for (int m = 0; m < K; ++m) {
-                    W.ckey[(long long)m * W.crows + row] = top.key[m];
-                    W.cgam[(long long)m * W.crows + row] = top.e[m];
-                }
+                for (int m = 0; m < K; ++m) W.ckey[(long long)m * W.crows + row] = top.key[m];
             }
         }
     }
-    // front to back: weights T_m gamma_m (Eq. 6-7); gamma came with the key.
-    // Descriptor loads go out four slots at a time; unused slots read
-    // descriptor row 0, a valid address whose value is ignored.
+    // The kept fragments' low key words (point index, layer); empty slots 0.
+    unsigned lo[K];
+#pragma unroll
+    for (int m = 0; m < K; ++m) {
+        lo[m] = m < nk ? (unsigned)(top.key[m] & 0xFFFFFFFFull) : 0u;
+        if (!TP_IN_RANGE(W.status, (lo[m] >> 4) < (unsigned long long)W.n_points)) lo[m] = 0u;
+    }
+    // Each kept fragment's opacity gamma = beta iota alpha (Eq. 3) from its
+    // point's record, at its own layer and pixel, in the order of the list
+    // build's float32 operations; the loads go out four slots at a time
+    // (unused slots read point 0, a valid address whose value is ignored).
     constexpr int NB = 4;
+    const float4 *__restrict__ rec = W.rec + (long long)v * W.n_points;
     float wgt[K];
+#pragma unroll
+    for (int m0 = 0; m0 < K; m0 += NB) {
+#pragma unroll
+        for (int u = 0; u < NB; ++u) wgt[m0 + u] = 0.0f;
+        if (m0 >= nk_warp) continue;
+        float4 r[NB];
+        float al[NB];
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            r[u] = rec[lo[m0 + u] >> 4];
+            al[u] = __ldg(W.opacity + (lo[m0 + u] >> 4));
+        }
+#pragma unroll
+        for (int u = 0; u < NB; ++u) {
+            if (m0 + u < nk) {
+                const int Lf = (int)(lo[m0 + u] & 15u), d = Lf - L;
+                const FragW w = frag_weights(F, r[u].x, r[u].y, r[u].w, Lf, j >> d, k >> d);
+                wgt[m0 + u] = w.wx * w.wy * w.iota * al[u];
+            }
+        }
+    }
+    if (out_ok && F.coarse && L > 0) {  // the backward of coarse-layer inclusion reads the parents' opacities
+        const long long row = coarse_row(B, v, L, j, k);
+        if (TP_IN_RANGE(W.status, row >= 0 && row < W.crows)) {
+#pragma unroll
+            for (int m = 0; m < K; ++m) W.cgam[(long long)m * W.crows + row] = __float_as_uint(wgt[m]);
+        }
+    }
+    // front to back: weights T_m gamma_m (Eq. 6-7), in place of the opacities
     float T = 1.0f;
 #pragma unroll
     for (int m = 0; m < K; ++m) {
-        wgt[m] = 0.0f;
         if (m >= nk_warp) break;
         if (m < nk) {
-            const float gam = __uint_as_float(top.e[m]);
+            const float gam = wgt[m];
             wgt[m] = T * gam;
             T = T * (1.0f - gam);
         }
     }
-    // descriptor rows of the kept points (empty slots: row 0); the keys are dead from here
+    // descriptor rows of the kept points (empty slots: row 0)
     unsigned row[K];
 #pragma unroll
-    for (int m = 0; m < K; ++m) {
-        row[m] = m < nk ? key_point(top.key[m]) : 0u;
-        if (!TP_IN_RANGE(W.status, row[m] < (unsigned long long)W.n_points || m >= nk)) row[m] = 0u;
-    }
+    for (int m = 0; m < K; ++m) row[m] = lo[m] >> 4;
     const int D = F.D;
     constexpr int G = DescGroup<DescT>::G;
     for (int d0 = 0; d0 < D; d0 += G) {

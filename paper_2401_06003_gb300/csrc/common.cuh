@@ -128,6 +128,11 @@ struct Workspace {
     long long crows;
     long long n_points;     // points of the frame (index checks of the checking build)
     unsigned capacity;
+    // the frame's point records [views][n] (x, y, z, s) and opacities [n]
+    // (caller buffers, read by the blend: it recomputes each kept fragment's
+    // opacity gamma from its point)
+    const float4 *rec;
+    const float *opacity;
 };
 
 // ---------------------------------------------------------------------------

@@ -67,7 +67,7 @@ tp_status tp_render_forward_static(const tp_config *cfg, const tp_camera *cam, i
     if (s != TP_OK) return s;
     s = tp_splat_forward(cfg, cam, n, records, opacity, ws, need, stream);
     if (s != TP_OK) return s;
-    s = tp_blend(cfg, cam, n, desc, pyramid, nullptr, nullptr, nullptr, nullptr, ws, need, stream);
+    s = tp_blend(cfg, cam, n, records, opacity, desc, pyramid, nullptr, nullptr, nullptr, nullptr, ws, need, stream);
     if (s != TP_OK || !device_flags) return s;
     // The status word is the workspace's first 4 bytes.
     if (cudaMemcpyAsync(device_flags, ws, sizeof(uint32_t), cudaMemcpyDeviceToDevice, (cudaStream_t)stream) !=

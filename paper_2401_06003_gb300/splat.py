@@ -143,7 +143,10 @@ class Renderer:
                                        _ptr(opacity), _ptr(ws), ws.numel(), _stream(self.device))
         _lib.check("tp_splat_forward", st)
 
-    def blend(self, n, desc, ws, store_lists=False, stats=False, pyramid=None):
+    def blend(self, records, opacity, desc, ws, store_lists=False, stats=False, pyramid=None):
+        n = records.shape[0]
+        _need(records, torch.float32, (n, 4), "records", self.device)
+        _need(opacity, torch.float32, (n,), "opacity", self.device)
         _need(desc, self.desc_dtype, (n, self.D), "desc", self.device)
         dev = self.device
         if pyramid is None:
@@ -155,9 +158,9 @@ class Renderer:
         if stats:
             t_final = torch.empty((self.P,), dtype=torch.float32, device=dev)
             n_frag = torch.empty((self.P,), dtype=torch.int32, device=dev)
-        st = self.lib.tp_blend(ctypes.byref(self.cfg), ctypes.byref(self.cam), n, _ptr(desc), _ptr(pyramid),
-                               _ptr(kept), _ptr(n_kept), _ptr(t_final), _ptr(n_frag), _ptr(ws), ws.numel(),
-                               _stream(dev))
+        st = self.lib.tp_blend(ctypes.byref(self.cfg), ctypes.byref(self.cam), n, _ptr(records), _ptr(opacity),
+                               _ptr(desc), _ptr(pyramid), _ptr(kept), _ptr(n_kept), _ptr(t_final), _ptr(n_frag),
+                               _ptr(ws), ws.numel(), _stream(dev))
         _lib.check("tp_blend", st)
         return pyramid, kept, n_kept, t_final, n_frag
 
@@ -229,7 +232,7 @@ class Renderer:
             ws = self.new_workspace(n)
         records = self.project(pos, size_w, ws)
         self.splat_forward(records, opacity, ws)
-        pyramid, kept, n_kept, t_final, n_frag = self.blend(n, desc, ws, store_lists, stats)
+        pyramid, kept, n_kept, t_final, n_frag = self.blend(records, opacity, desc, ws, store_lists, stats)
         return Frame(pyramid, records, ws, kept, n_kept, t_final, n_frag)
 
     def backward(self, frame: Frame, opacity, desc, grad_pyramid):
@@ -346,7 +349,10 @@ class BatchRenderer:
                                              _stream(self.device))
         _lib.check("tp_batch_splat_forward", st)
 
-    def blend(self, n, desc, ws, store_lists=False, stats=False, pyramid=None):
+    def blend(self, records, opacity, desc, ws, store_lists=False, stats=False, pyramid=None):
+        n = records.shape[1]
+        _need(records, torch.float32, (self.n_views, n, 4), "records", self.device)
+        _need(opacity, torch.float32, (n,), "opacity", self.device)
         _need(desc, self.desc_dtype, (n, self.D), "desc", self.device)
         dev = self.device
         if pyramid is None:
@@ -358,8 +364,9 @@ class BatchRenderer:
         if stats:
             t_final = torch.empty((self.P,), dtype=torch.float32, device=dev)
             n_frag = torch.empty((self.P,), dtype=torch.int32, device=dev)
-        st = self.lib.tp_batch_blend(*self._common(), n, _ptr(desc), _ptr(pyramid), _ptr(kept), _ptr(n_kept),
-                                     _ptr(t_final), _ptr(n_frag), _ptr(ws), ws.numel(), _stream(dev))
+        st = self.lib.tp_batch_blend(*self._common(), n, _ptr(records), _ptr(opacity), _ptr(desc), _ptr(pyramid),
+                                     _ptr(kept), _ptr(n_kept), _ptr(t_final), _ptr(n_frag), _ptr(ws), ws.numel(),
+                                     _stream(dev))
         _lib.check("tp_batch_blend", st)
         return pyramid, kept, n_kept, t_final, n_frag
 
@@ -406,7 +413,7 @@ class BatchRenderer:
             ws = self.new_workspace(n)
         records = self.project(pos, size_w, ws)
         self.splat_forward(records, opacity, ws)
-        pyramid, kept, n_kept, t_final, n_frag = self.blend(n, desc, ws, store_lists, stats)
+        pyramid, kept, n_kept, t_final, n_frag = self.blend(records, opacity, desc, ws, store_lists, stats)
         return Frame(pyramid, records, ws, kept, n_kept, t_final, n_frag)
 
     def backward(self, frame: Frame, opacity, desc, grad_pyramid):
@@ -456,7 +463,7 @@ def autotune_tiles(cameras, n_layers, pos, size_w, opacity, desc, K=16, candidat
                     e0.record()
                     r.project(pos, size_w, ws, records=rec)
                     r.splat_forward(rec, opacity, ws)
-                    r.blend(n, desc, ws, pyramid=pyr)
+                    r.blend(rec, opacity, desc, ws, pyramid=pyr)
                     r.splat_backward(rec, opacity, desc, G, ws, grads=grads)
                     e1.record()
                     torch.cuda.synchronize()
@@ -520,7 +527,7 @@ def autotune_batch_tiles(cameras, n_layers, pos, size_w, opacity, desc, K=16, ca
                 e0.record()
                 br.project(pos, size_w, ws, records=rec)
                 br.splat_forward(rec, opacity, ws)
-                br.blend(n, desc, ws, pyramid=pyr)
+                br.blend(rec, opacity, desc, ws, pyramid=pyr)
                 br.splat_backward(rec, opacity, desc, G, ws, grads=grads)
                 e1.record()
                 torch.cuda.synchronize()

@@ -87,7 +87,7 @@ def test_batch_step_replays_as_one_cuda_graph(scene):
     def step():
         br.project(pos, sw, ws, records=rec)
         br.splat_forward(rec, op, ws)
-        br.blend(n, desc, ws, pyramid=pyr)
+        br.blend(rec, op, desc, ws, pyramid=pyr)
         br.splat_backward(rec, op, desc, G, ws, grads=grads)
 
     s = torch.cuda.Stream(device())
