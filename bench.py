@@ -693,7 +693,7 @@ def run_batch(args):
     ms_per_step = total_ms / args.steps
     value = V * N * world / (ms_per_step * 1e-3) / 1e6
 
-    # per-view latency: each view rendered alone (forward + backward), same tiles
+    # context for the batch: each view rendered alone (forward + backward), same tiles
     per_view = []
     for v, cam in enumerate(sc.cameras):
         r = Renderer(cam, sc.n_layers, K=sc.K, D=D, tile=tiles[v], device=dev)
@@ -731,9 +731,16 @@ def run_batch(args):
                        "l2": "inputs larger than L2; no flush"},
             "batch_step_ms": {"p50": round(float(np.percentile(step_ms, 50)), 4),
                               "p99": round(float(np.percentile(step_ms, 99)), 4)},
-            "per_view": per_view,
-            "per_view_p50_ms": round(float(np.percentile([p["p50_ms"] for p in per_view], 50)), 4),
-            "per_view_p99_ms": round(float(np.percentile([p["p99_ms"] for p in per_view], 99)), 4),
+            # inside the batch every stage is one launch over all views, so each
+            # view's outputs are complete when the step's last launch ends: a
+            # view's latency in the batch is the batch step's (events per replay)
+            "per_view_in_batch_ms": {"p50": round(float(np.percentile(step_ms, 50)), 4),
+                                     "p99": round(float(np.percentile(step_ms, 99)), 4),
+                                     "amortised": round(ms_per_step / V, 4)},
+            # context: each view rendered alone with the same tiles (not a batch measurement)
+            "single_view": per_view,
+            "single_view_p50_ms": round(float(np.percentile([p["p50_ms"] for p in per_view], 50)), 4),
+            "single_view_p99_ms": round(float(np.percentile([p["p99_ms"] for p in per_view], 99)), 4),
             "sum_of_single_view_p50_ms": round(sum(p["p50_ms"] for p in per_view), 4),
             "autotune": {"seconds": round(tune_s, 2),
                          "ms_by_resolution": {f"{w}x{h}": {f"{a}x{b}": round(t, 4) for (a, b), t in d.items()}

@@ -422,7 +422,9 @@ class BatchRenderer:
                                    frame.kept if use_lists else None, frame.n_kept if use_lists else None)
 
 
-TILE_CANDIDATES = ((16, 8), (16, 16), (32, 8), (8, 16), (8, 8))
+# screen tiles the autotuners time: 64 to 512 pixels, square and wide shapes
+TILE_CANDIDATES = ((16, 8), (16, 16), (32, 8), (8, 16), (8, 8), (32, 4), (16, 4), (24, 8), (16, 12), (32, 16),
+                   (64, 4))
 
 
 def autotune_tiles(cameras, n_layers, pos, size_w, opacity, desc, K=16, candidates=TILE_CANDIDATES, iters=3,
