@@ -308,6 +308,10 @@ def run_ours(args):
              torch.empty((N, D), device=dev))
     store = args.mode == "store"
     stream = torch.cuda.current_stream(dev)
+    # the gradient buffers are cleared on a second stream while the blend runs
+    # (it uses little DRAM bandwidth); the backward waits for the clearing
+    zero_stream = torch.cuda.Stream(dev)
+    zeroed = torch.cuda.Event()
 
     def step(ev=None):
         if ev is not None:
@@ -318,10 +322,15 @@ def run_ours(args):
         r.splat_forward(rec, op, ws)
         if ev is not None:
             ev[2].record(stream)
+        zero_stream.wait_stream(stream)  # also orders it after the previous step's backward
+        r.zero_gradients(grads, stream=zero_stream)
+        zeroed.record(zero_stream)
         _, kept, nk, _, _ = r.blend(rec, op, desc, ws, store_lists=store, pyramid=pyr)
         if ev is not None:
             ev[3].record(stream)
-        r.splat_backward(rec, op, desc, G, ws, kept if store else None, nk if store else None, grads=grads)
+        stream.wait_event(zeroed)
+        r.splat_backward(rec, op, desc, G, ws, kept if store else None, nk if store else None, grads=grads,
+                         grads_zeroed=True)
         if ev is not None:
             ev[4].record(stream)
 

@@ -148,7 +148,7 @@ typedef struct {
     int32_t mode;       /* TP_STORE_LISTS or TP_RECOMPUTE (see tp_splat_backward) */
     int32_t tile_w;     /* screen tile of the binning and blend kernels, in pixels */
     int32_t tile_h;     /*   of each layer; 0 = the default 16 x 8 */
-    int32_t flags;      /* TP_COARSE_LAYERS or 0 */
+    int32_t flags;      /* TP_COARSE_LAYERS | TP_GRADS_ZEROED, or 0 */
 } tp_config;
 
 /*
@@ -165,6 +165,14 @@ typedef struct {
  * lists, whose point indices do not say which layer's fragment was kept).
  */
 #define TP_COARSE_LAYERS 0x1
+
+/*
+ * tp_config.flags.  TP_GRADS_ZEROED: the backward calls take their gradient
+ * buffers as already zero (the caller cleared them, for example on another
+ * stream while the forward kernels run, ordered before the call) and only
+ * add to them; without it they clear the buffers first on `stream`.
+ */
+#define TP_GRADS_ZEROED 0x2
 
 /*
  * Number of pyramid pixels P = sum_L W_L H_L.  If layer_offsets is not NULL
@@ -400,6 +408,15 @@ TP_API tp_status tp_batch_splat_backward(const tp_config *cfg, const tp_camera *
                                          const float *grad_pyramid, float *grad_pos, float *grad_size_w,
                                          float *grad_opacity, float *grad_desc, void *ws, int64_t ws_bytes,
                                          tp_stream_t stream);
+
+/*
+ * Clears the gradient buffers of tp_splat_backward (the same layouts: with
+ * grad_size_w NULL grad_pos is the packed [n][4] form) on `stream`, so that a
+ * caller can clear them on a second stream while the forward kernels run and
+ * call the backward with TP_GRADS_ZEROED.  cudaMemsetAsync only; no kernel.
+ */
+TP_API tp_status tp_zero_gradients(const tp_config *cfg, int64_t n, float *grad_pos, float *grad_size_w,
+                                   float *grad_opacity, float *grad_desc, tp_stream_t stream);
 
 /*
  * The batch backward (lists recomputed) that also returns the gradient of

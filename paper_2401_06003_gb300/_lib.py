@@ -21,7 +21,7 @@ HEADER = os.path.join(_build.INCLUDE, "trips.h")
 TP_FLAG_NONFINITE, TP_FLAG_CAPACITY, TP_FLAG_TIMEOUT, TP_FLAG_BOUNDS = 0x1, 0x2, 0x4, 0x8
 TP_F32, TP_BF16 = 0, 1
 TP_STORE_LISTS, TP_RECOMPUTE = 0, 1
-TP_COARSE_LAYERS = 0x1
+TP_COARSE_LAYERS, TP_GRADS_ZEROED = 0x1, 0x2
 
 
 class tp_camera(ctypes.Structure):
@@ -70,6 +70,7 @@ _SIGS = {
                                                _P, _P, _P, _P, _P, _P, _P, _P, _I64, _P]),
     "tp_batch_splat_backward_cameras": (ctypes.c_int, [ctypes.POINTER(tp_config), _P, _P, ctypes.c_int32, _I64,
                                                        _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _I64, _P]),
+    "tp_zero_gradients": (ctypes.c_int, [ctypes.POINTER(tp_config), _I64, _P, _P, _P, _P, _P]),
     "tp_camera_backward": (ctypes.c_int, [ctypes.POINTER(tp_camera), _I64, _P, _P, _P, _P, _P, _P]),
     "tp_init_sizes_workspace_bytes": (_I64, [_I64]),
     "tp_init_point_sizes": (ctypes.c_int, [_I64, _P, _P, _P, _I64, _P]),

@@ -57,7 +57,7 @@ tp_status check_config(const tp_config *cfg)
     if (cfg->K < 1 || cfg->K > 255) return TP_ERR_INVALID_ARG;
     if (cfg->K != 4 && cfg->K != 8 && cfg->K != 16 && cfg->K != 32) return TP_ERR_UNSUPPORTED;
     if (cfg->tile_w < 0 || cfg->tile_h < 0) return TP_ERR_INVALID_ARG;
-    if ((cfg->flags & ~TP_COARSE_LAYERS) != 0) return TP_ERR_INVALID_ARG;
+    if ((cfg->flags & ~(TP_COARSE_LAYERS | TP_GRADS_ZEROED)) != 0) return TP_ERR_INVALID_ARG;
     return TP_OK;
 }
 
@@ -84,6 +84,7 @@ tp_status make_frame(const tp_config *cfg, const tp_camera *cam, int tw, int th,
     F.tile_w = tw;
     F.tile_h = th;
     F.coarse = (cfg->flags & TP_COARSE_LAYERS) ? 1 : 0;
+    F.grads_zeroed = (cfg->flags & TP_GRADS_ZEROED) ? 1 : 0;
     fill_layers(cam, cfg->n_layers, F);
     int tiles = 0;
     for (int L = 0; L < F.n_layers; ++L) {
@@ -459,6 +460,23 @@ tp_status tp_batch_splat_backward_cameras(const tp_config *cfg, const tp_camera 
     return do_backward<kMaxViews>(cfg, cams, tiles, n_views, n, records, opacity, desc, nullptr, nullptr,
                                   grad_pyramid, grad_pos, grad_size_w, grad_opacity, grad_desc, ws, ws_bytes, stream,
                                   pos, grad_cameras);
+}
+
+tp_status tp_zero_gradients(const tp_config *cfg, int64_t n, float *grad_pos, float *grad_size_w,
+                            float *grad_opacity, float *grad_desc, tp_stream_t stream)
+{
+    if (check_config(cfg) != TP_OK || n < 0 || n >= kMaxPoints) return TP_ERR_INVALID_ARG;
+    if (n == 0) return TP_OK;
+    if (!grad_pos || !grad_opacity || !grad_desc) return TP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool pos4 = grad_size_w == nullptr;
+    const size_t N = (size_t)n;
+    if (cudaMemsetAsync(grad_pos, 0, sizeof(float) * (pos4 ? 4 : 3) * N, s) != cudaSuccess) return TP_ERR_CUDA;
+    if (!pos4 && cudaMemsetAsync(grad_size_w, 0, sizeof(float) * N, s) != cudaSuccess) return TP_ERR_CUDA;
+    if (cudaMemsetAsync(grad_opacity, 0, sizeof(float) * N, s) != cudaSuccess) return TP_ERR_CUDA;
+    if (cudaMemsetAsync(grad_desc, 0, sizeof(float) * (size_t)cfg->desc_dim * N, s) != cudaSuccess)
+        return TP_ERR_CUDA;
+    return TP_OK;
 }
 
 tp_status tp_get_status(const void *ws, tp_stream_t stream, int32_t *device_flags)

@@ -44,6 +44,7 @@ __global__ void __launch_bounds__(kBlock) k_project_count(const __grid_constant_
                                                           long long n, const float *__restrict__ pos,
                                                           const float *__restrict__ size_w, float4 *__restrict__ rec_all)
 {
+    allow_dependent_launch();
     const int v = MaxV > 1 ? (int)blockIdx.y : 0;
     const Frame &F = B.view[v];
     float4 *__restrict__ rec = rec_all + (long long)v * n;
@@ -71,6 +72,8 @@ __global__ void __launch_bounds__(kBlock) k_project_count(const __grid_constant_
 // cursor, and the tile's total goes to tile_off[t] for the offset scan.
 __global__ void __launch_bounds__(kBlock) k_tile_totals(int n_tiles, Workspace W)
 {
+    wait_previous_grid();
+    allow_dependent_launch();
     const int t = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (t >= n_tiles) return;
@@ -100,6 +103,8 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(int n_tiles, Workspace W)
 {
     __shared__ unsigned sv[kScanTile + kScanTile / kScanPer];
     __shared__ unsigned warp_tot[32];
+    wait_previous_grid();
+    allow_dependent_launch();
     const int T = n_tiles, tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     unsigned carry = 0;
@@ -159,6 +164,8 @@ __global__ void __launch_bounds__(kBlock) k_fill(const __grid_constant__ Batch<M
     const float4 *__restrict__ rec = rec_all + (long long)v * n;
     const unsigned *__restrict__ tile_off = W.tile_off + B.tile_base[v];
     unsigned *__restrict__ cursor = W.tile_cursor + (size_t)B.tile_base[v] * kCopies;
+    wait_previous_grid();
+    allow_dependent_launch();
     if (*((volatile unsigned *)W.status) & TP_FLAG_CAPACITY) return;  // the lists do not fit: outputs invalid
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -205,15 +212,13 @@ cudaError_t launch_scan_fill(const Batch<MaxV> &B, const Workspace &W, long long
                              const float *opacity, cudaStream_t stream)
 {
     const long long threads = (long long)B.n_tiles * 32;
-    k_tile_totals<<<(int)((threads + kBlock - 1) / kBlock), kBlock, 0, stream>>>(B.n_tiles, W);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_dependent(k_tile_totals, dim3((unsigned)((threads + kBlock - 1) / kBlock)), dim3(kBlock),
+                                     0, stream, B.n_tiles, W);
     if (e != cudaSuccess) return e;
-    k_scan_tiles<<<1, 1024, 0, stream>>>(B.n_tiles, W);
-    e = cudaGetLastError();
+    e = launch_dependent(k_scan_tiles, dim3(1), dim3(1024), 0, stream, B.n_tiles, W);
     if (e != cudaSuccess || n == 0) return e;
     const dim3 grid(grid_for(n), B.n_views);
-    k_fill<MaxV><<<grid, kBlock, 0, stream>>>(B, W, n, rec, opacity);
-    return cudaGetLastError();
+    return launch_dependent(k_fill<MaxV>, grid, dim3(kBlock), 0, stream, B, W, n, rec, opacity);
 }
 
 template cudaError_t launch_project_count<1>(const Batch<1> &, const Workspace &, long long, const float *,

@@ -377,6 +377,8 @@ __global__ void __maxnreg__(K <= 16 ? 80 : 168) k_tile_blend(const __grid_consta
                              unsigned *__restrict__ n_frag, int layer)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    wait_previous_grid();
+    allow_dependent_launch();
     if (*((volatile unsigned *)W.status) & TP_FLAG_CAPACITY) return;  // the lists were cut short: outputs invalid
     const int tile = block_tile(B, layer);  // global over the batch
     if (tile < 0) return;
@@ -636,6 +638,8 @@ __global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_backward(const __grid_con
                                 const float *__restrict__ pos, double *__restrict__ gcam)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    wait_previous_grid();
+    allow_dependent_launch();
     if (*((volatile unsigned *)W.status) & TP_FLAG_CAPACITY) return;  // the lists were cut short: outputs invalid
     const int tile = blockIdx.x;  // global over the batch
     const int v = view_of_tile(B, tile);
@@ -872,17 +876,16 @@ static cudaError_t blend_launches(const Batch<MaxV> &B, const Workspace &W, cons
     cudaError_t e = prepare_tile_kernel(k_tile_blend<K, DescT, MaxV, STATS>, smem, B.max_threads);
     if (e != cudaSuccess) return e;
     if (!B.view[0].coarse) {
-        k_tile_blend<K, DescT, MaxV, STATS><<<B.n_tiles, B.max_threads, smem, stream>>>(
-            B, W, desc, pyramid, kept, n_kept, t_final, n_frag, -1);
-        return cudaGetLastError();
+        return launch_dependent(k_tile_blend<K, DescT, MaxV, STATS>, dim3(B.n_tiles), dim3(B.max_threads), smem,
+                                stream, B, W, desc, pyramid, kept, n_kept, t_final, n_frag, -1);
     }
     for (int L = B.view[0].n_layers - 1; L >= 0; --L) {
         int tiles = 0;
         for (int v = 0; v < B.n_views; ++v) tiles += B.view[v].tile_base[L + 1] - B.view[v].tile_base[L];
         if (tiles == 0) continue;
-        k_tile_blend<K, DescT, MaxV, STATS><<<tiles, B.max_threads, smem, stream>>>(
-            B, W, desc, pyramid, kept, n_kept, t_final, n_frag, L);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        e = launch_dependent(k_tile_blend<K, DescT, MaxV, STATS>, dim3(tiles), dim3(B.max_threads), smem, stream, B,
+                             W, desc, pyramid, kept, n_kept, t_final, n_frag, L);
+        if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
@@ -915,9 +918,9 @@ static cudaError_t backward_launch(const Batch<MaxV> &B, const Workspace &W, con
     if (CAM) smem += 16 * sizeof(float) * (size_t)B.max_threads;
     cudaError_t e = prepare_tile_kernel(k_tile_backward<K, DescT, MaxV, DC, CAM>, smem, B.max_threads);
     if (e != cudaSuccess) return e;
-    k_tile_backward<K, DescT, MaxV, DC, CAM><<<B.n_tiles, B.max_threads, smem, stream>>>(
-        B, W, d, a.grad_pyr, a.gpos, a.gsw, a.gop, a.gdesc, a.n, a.rec, a.opacity, a.pos, a.gcam);
-    return cudaGetLastError();
+    return launch_dependent(k_tile_backward<K, DescT, MaxV, DC, CAM>, dim3(B.n_tiles), dim3(B.max_threads), smem,
+                            stream, B, W, d, a.grad_pyr, a.gpos, a.gsw, a.gop, a.gdesc, a.n, a.rec, a.opacity, a.pos,
+                            a.gcam);
 }
 
 template <int K, typename DescT, int MaxV>
@@ -987,12 +990,14 @@ cudaError_t launch_backward(const Batch<MaxV> &B, const Workspace &W, long long 
     if (n == 0) return cudaSuccess;
     const int K = B.view[0].K, D = B.view[0].D;
     const bool pos4 = B.view[0].pos4 != 0;
-    if ((e = cudaMemsetAsync(grad_pos, 0, sizeof(float) * (pos4 ? 4 : 3) * (size_t)n, stream)) != cudaSuccess)
-        return e;
-    if (!pos4 && (e = cudaMemsetAsync(grad_sw, 0, sizeof(float) * (size_t)n, stream)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(grad_opacity, 0, sizeof(float) * (size_t)n, stream)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(grad_desc, 0, sizeof(float) * (size_t)D * (size_t)n, stream)) != cudaSuccess)
-        return e;
+    if (!B.view[0].grads_zeroed) {
+        if ((e = cudaMemsetAsync(grad_pos, 0, sizeof(float) * (pos4 ? 4 : 3) * (size_t)n, stream)) != cudaSuccess)
+            return e;
+        if (!pos4 && (e = cudaMemsetAsync(grad_sw, 0, sizeof(float) * (size_t)n, stream)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(grad_opacity, 0, sizeof(float) * (size_t)n, stream)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(grad_desc, 0, sizeof(float) * (size_t)D * (size_t)n, stream)) != cudaSuccess)
+            return e;
+    }
     const BwdArgs a{grad_pyramid, grad_pos, grad_sw, grad_opacity, grad_desc, n, rec, opacity, pos, grad_cameras};
     if (desc_dtype == TP_BF16) {
         TPK_DISPATCH_K(K, return (backward_impl<KC, __nv_bfloat16, MaxV>(B, W, desc, kept, n_kept, a, stream)));

@@ -37,6 +37,7 @@ struct Frame {
     int desc_vec;          // 1 if descriptors can be read 4 channels at a time
     int grad_vec;          // 1 if descriptor gradients can take 4-channel vector atomics
     int pos4;              // 1: position gradients are [n][4] rows (X, Y, Z, s_w), one vector atomic each
+    int grads_zeroed;      // 1: the caller cleared the gradient buffers (no memsets in the backward)
     int coarse;            // 1: coarse-layer inclusion (a pixel's list also holds the fragments of
                            //    the coarser-layer pixels that contain it, Sec. 3.6)
     int lw[kMaxLayers], lh[kMaxLayers];            // layer sizes W_L, H_L
@@ -330,6 +331,33 @@ template <>
 __device__ __forceinline__ float load_desc<__nv_bfloat16>(const __nv_bfloat16 *p)
 {
     return __bfloat162float(*p);
+}
+
+// ---------------------------------------------------------------------------
+// Programmatic dependent launch: a kernel launched by launch_dependent may be
+// scheduled while the previous kernel of its stream is still finishing; it
+// calls wait_previous_grid() before it touches anything that kernel wrote,
+// and allow_dependent_launch() to let the next kernel be scheduled early.
+// Both are no-ops for a kernel launched the ordinary way.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void wait_previous_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_dependent_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                                    Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
 }
 
 // ---------------------------------------------------------------------------

@@ -48,6 +48,15 @@ def _grad_buffers(n, D, dev, grads):
     return (gp, gs, go, gd), (gp, gs, go, gd)
 
 
+def _backward_cfg(cfg, grads_zeroed):
+    """The frame's config, with TP_GRADS_ZEROED when the caller cleared the gradients."""
+    if not grads_zeroed:
+        return ctypes.byref(cfg)
+    c = _lib.tp_config.from_buffer_copy(cfg)
+    c.flags |= _lib.TP_GRADS_ZEROED
+    return ctypes.byref(c)
+
+
 def _packed_pos_size(grad_pos, grad_size_w):
     """The packed [n, 4] base of (grad_pos, grad_size_w) views, or None."""
     n = grad_pos.shape[0]
@@ -164,16 +173,32 @@ class Renderer:
         _lib.check("tp_blend", st)
         return pyramid, kept, n_kept, t_final, n_frag
 
-    def splat_backward(self, records, opacity, desc, grad_pyramid, ws, kept=None, n_kept=None, grads=None):
+    def splat_backward(self, records, opacity, desc, grad_pyramid, ws, kept=None, n_kept=None, grads=None,
+                       grads_zeroed=False):
+        """Point gradients of sum(grad_pyramid * pyramid).  ``grads_zeroed``: the
+        caller's ``grads`` buffers are already zero (cleared, e.g., on another
+        stream during the forward kernels), so the call only adds to them."""
         n = records.shape[0]
         dev = self.device
         _need(grad_pyramid, torch.float32, (self.P, self.D), "grad_pyramid", dev)
+        if grads_zeroed and grads is None:
+            raise ValueError("grads_zeroed needs the caller's gradient buffers")
         (gp, gs, go, gd), out = _grad_buffers(n, self.D, dev, grads)
-        st = self.lib.tp_splat_backward(ctypes.byref(self.cfg), ctypes.byref(self.cam), n, _ptr(records),
-                                        _ptr(opacity), _ptr(desc), _ptr(kept), _ptr(n_kept), _ptr(grad_pyramid),
+        st = self.lib.tp_splat_backward(_backward_cfg(self.cfg, grads_zeroed), ctypes.byref(self.cam), n,
+                                        _ptr(records), _ptr(opacity), _ptr(desc), _ptr(kept), _ptr(n_kept), _ptr(grad_pyramid),
                                         _ptr(gp), _ptr(gs), _ptr(go), _ptr(gd), _ptr(ws), ws.numel(), _stream(dev))
         _lib.check("tp_splat_backward", st)
         return out
+
+    def zero_gradients(self, grads, stream=None):
+        """Clears gradient buffers (as splat_backward takes them) on ``stream``
+        (default: the current stream), for a later call with grads_zeroed=True."""
+        gp, gs, go, gd = grads
+        n = gp.shape[0]
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        st = self.lib.tp_zero_gradients(ctypes.byref(self.cfg), n, _ptr(gp), _ptr(gs), _ptr(go), _ptr(gd),
+                                        ctypes.c_void_p(s.cuda_stream))
+        _lib.check("tp_zero_gradients", st)
 
     def camera_backward(self, pos, records, grad_pos, grad_size_w, out=None) -> torch.Tensor:
         """dL/d(fx, fy, cx, cy, R[0..8], t[0..2]) [16] float64, from this view's point gradients."""

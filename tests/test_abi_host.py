@@ -37,6 +37,15 @@ def test_checking_build_exports_every_declared_symbol():
     assert dbg.tp_status_string(_lib.TP_ERR_BOUNDS).decode().startswith("out-of-range")
 
 
+def test_zero_gradients_host_checks(lib):
+    cfg = _lib.make_config(4, 16, 4)
+    assert lib.tp_zero_gradients(ctypes.byref(cfg), 0, None, None, None, None, None) == _lib.TP_OK
+    assert lib.tp_zero_gradients(ctypes.byref(cfg), 10, None, None, None, None, None) == _lib.TP_ERR_INVALID_ARG
+    assert lib.tp_zero_gradients(ctypes.byref(cfg), -1, None, None, None, None, None) == _lib.TP_ERR_INVALID_ARG
+    bad = _lib.make_config(4, 16, 4, flags=0x4)
+    assert lib.tp_zero_gradients(ctypes.byref(bad), 0, None, None, None, None, None) == _lib.TP_ERR_INVALID_ARG
+
+
 def test_struct_layout_matches_header():
     assert ctypes.sizeof(_lib.tp_camera) == 17 * 4 + 2 * 4
     assert ctypes.sizeof(_lib.tp_config) == 9 * 4
@@ -56,7 +65,7 @@ def test_coarse_layer_flag(lib):
         a = lib.tp_workspace_bytes(ctypes.byref(plain), ctypes.byref(cam), 1000, 0)
         b = lib.tp_workspace_bytes(ctypes.byref(coarse), ctypes.byref(cam), 1000, 0)
         assert 0 <= (b - a) - 12 * K * coarse_pix < 512, (K, a, b)
-    bad = _lib.make_config(4, 16, 4, flags=0x2)
+    bad = _lib.make_config(4, 16, 4, flags=0x4)
     assert lib.tp_workspace_bytes(ctypes.byref(bad), ctypes.byref(cam), 10, 0) == -1
     coarse = _lib.make_config(4, 16, 4, mode=_lib.TP_STORE_LISTS, flags=_lib.TP_COARSE_LAYERS)
     need = lib.tp_workspace_bytes(ctypes.byref(coarse), ctypes.byref(cam), 10, 0)

@@ -383,3 +383,23 @@ def test_packed_and_separate_gradient_layouts_agree(cube):
         cb = r.camera_backward(ins[0], fr.records, separate[0], separate[1]).cpu().numpy()
         assert_close_scaled(ca, cb, 1e-4, name=f"{mode} camera gradient from packed rows",
                             segments=[(0, 4), (4, 13), (13, 16)])
+
+
+def test_gradients_cleared_on_another_stream(cube):
+    """TP_GRADS_ZEROED: buffers cleared by tp_zero_gradients on a second stream
+    (ordered before the call) give the gradients of the default path."""
+    n, D = cube.n, cube.D
+    r, fr, ins, _ = gpu_frame(cube, mode="recompute")
+    G = to_dev(np.random.default_rng(27).uniform(-1, 1, (r.P, D)).astype(np.float32))
+    ref = [t.cpu().numpy() for t in r.splat_backward(fr.records, ins[2], ins[3], G, fr.workspace)]
+    grads = (torch.full((n, 4), 7.0, device=device()), None, torch.full((n,), 7.0, device=device()),
+             torch.full((n, D), 7.0, device=device()))
+    side = torch.cuda.Stream(device())
+    side.wait_stream(torch.cuda.current_stream(device()))
+    r.zero_gradients(grads, stream=side)
+    done = torch.cuda.Event()
+    done.record(side)
+    torch.cuda.current_stream(device()).wait_event(done)
+    got = r.splat_backward(fr.records, ins[2], ins[3], G, fr.workspace, grads=grads, grads_zeroed=True)
+    for a, b, name in zip(got, ref, ("pos", "size_w", "opacity", "desc")):
+        assert_close_scaled(a.cpu().numpy().reshape(n, -1), b.reshape(n, -1), 1e-4, name=f"pre-cleared grad_{name}")
