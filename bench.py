@@ -581,8 +581,13 @@ def run_ours(args):
         k1.record(stream)
         torch.cuda.synchronize(dev)
         knn_ms = max_over_ranks(k0.elapsed_time(k1), world, dev) / reps
+        # algorithmic bytes: read every position once (12 N) and write every size (4 N);
+        # the search itself is hash-grid lookups and distance arithmetic
+        knn_bytes = 16 * N
         size_init = {"ms": round(knn_ms, 3), "mpoints_s": round(N / (knn_ms * 1e-3) / 1e6, 1), "k": 4,
-                     "workspace_mb": round(kws.numel() / 1e6, 1)}
+                     "workspace_mb": round(kws.numel() / 1e6, 1), "algorithmic_bytes": knn_bytes,
+                     "frac": round(knn_bytes / (knn_ms * 1e-3) / 1e9 / peak, 5),
+                     "bound": "latency (random hash-grid lookups) and ALU, not HBM"}
         del kws
 
         merge = {"launches": sc.n_layers, "ms": round(mf_ms, 4), "algorithmic_bytes": mf_bytes,
