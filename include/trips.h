@@ -301,7 +301,11 @@ TP_API tp_status tp_camera_backward(const tp_camera *cam, int64_t n, const float
  * tp_merge_backward: from dL/d(image) grad_image [W H][D] (device), writes
  *   grad_pyramid [P][D] = dL/dP (dL/dP_L = dL/dM_L, dL/dM_{L+1} =
  *   up2^T dL/dM_L).  grad_image may be grad_pyramid's first rows.
- * 1 <= D <= 64; one kernel launch per layer.
+ * 1 <= D <= 64.  tp_merge out of place on up to 2^23 values of layer 0
+ * (W H D) is one kernel launch (each CTA merges a 32 x 32 tile of the image
+ * and the coarser pixels above it, recomputing a one-pixel halo); larger or
+ * in place, and tp_merge_backward, one launch per layer.  Both forms give the
+ * same bits.
  */
 TP_API tp_status tp_merge(const tp_camera *cam, int32_t n_layers, int32_t D, const float *pyramid, float *merged,
                           tp_stream_t stream);
