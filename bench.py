@@ -403,19 +403,24 @@ def run_ours(args):
         d_gr = [list(grads), [None if g is None else torch.empty_like(g) for g in grads]]
         h_out = [[torch.empty(g.shape, dtype=torch.float32).pin_memory() for g in grads if g is not None]
                  for _ in range(2)]
+        # the step's result read back: the loss <G, pyramid> whose gradient is the
+        # upstream gradient G (the point gradients stay on the device, as for an
+        # optimizer step); a second figure also downloads every gradient
+        d_loss = torch.empty((), dtype=torch.float32, device=dev)
+        h_loss = [torch.empty((), dtype=torch.float32).pin_memory() for _ in range(2)]
         h2d = sum(t.numel() * t.element_size() for t in h_in)
-        d2h = sum(t.numel() * t.element_size() for t in h_out[0])
+        d2h_grads = sum(t.numel() * t.element_size() for t in h_out[0])
         s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
         computed = [torch.cuda.Event() for _ in range(2)]
         downloaded = [torch.cuda.Event() for _ in range(2)]
         uploaded = [torch.cuda.Event() for _ in range(2)]
 
-        def pipeline(steps):
+        def pipeline(steps, download_grads):
             for k in range(steps):
                 b = k % 2
                 if k >= 2:
                     s_in.wait_event(computed[b])      # step k-2 no longer reads these inputs
-                    stream.wait_event(downloaded[b])  # its gradients are on the host
+                    stream.wait_event(downloaded[b])  # its results are on the host
                 with torch.cuda.stream(s_in):
                     for d_, h_ in zip(d_in[b], h_in):
                         d_.copy_(h_, non_blocking=True)
@@ -425,31 +430,43 @@ def run_ours(args):
                 r.project(pb, swb, ws, records=rec)
                 r.splat_forward(rec, opb, ws)
                 _, kept_b, nk_b, _, _ = r.blend(rec, opb, db, ws, store_lists=store, pyramid=pyr)
+                torch.dot(pyr.view(-1), G.view(-1), out=d_loss)
                 r.splat_backward(rec, opb, db, G, ws, kept_b if store else None, nk_b if store else None,
                                  grads=tuple(d_gr[b]))
                 computed[b].record(stream)
                 s_out.wait_event(computed[b])
                 with torch.cuda.stream(s_out):
-                    for h_, g_ in zip(h_out[b], [g for g in d_gr[b] if g is not None]):
-                        h_.copy_(g_, non_blocking=True)
+                    h_loss[b].copy_(d_loss, non_blocking=True)
+                    if download_grads:
+                        for h_, g_ in zip(h_out[b], [g for g in d_gr[b] if g is not None]):
+                            h_.copy_(g_, non_blocking=True)
                     downloaded[b].record(s_out)
             stream.wait_stream(s_out)
 
-        pipeline(min(args.warmup, 3))
-        torch.cuda.synchronize(dev)
-        barrier(world, dev)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        s_in.wait_stream(stream)
-        pipeline(args.steps)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        barrier(world, dev)
-        e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev) / args.steps
+        def timed_pipeline(download_grads):
+            pipeline(min(args.warmup, 3), download_grads)
+            torch.cuda.synchronize(dev)
+            barrier(world, dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s_in.wait_stream(stream)
+            pipeline(args.steps, download_grads)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            barrier(world, dev)
+            return max_over_ranks(e0.elapsed_time(e1), world, dev) / args.steps
+
+        e2e_ms = timed_pipeline(False)
+        e2e_grads_ms = timed_pipeline(True)
         e2e = {"value": round(N * world / (e2e_ms * 1e-3) / 1e6, 3), "unit": "Mpoints/s",
-               "ms_per_step": round(e2e_ms, 4), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "overlap": "double-buffered: uploads and downloads on two copy streams overlap the kernels"}
+               "ms_per_step": round(e2e_ms, 4), "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(h_loss[0].numel() * h_loss[0].element_size()),
+               "result": "the loss <G, pyramid> (G is its gradient); point gradients stay on the device",
+               "overlap": "double-buffered: uploads on a copy stream overlap the kernels",
+               "with_gradients_downloaded": {
+                   "value": round(N * world / (e2e_grads_ms * 1e-3) / 1e6, 3), "ms_per_step": round(e2e_grads_ms, 4),
+                   "d2h_bytes_per_step": int(d2h_grads + 4)}}
 
     # forward-only time (same frame, no backward), for the forward ms/frame figure
     torch.cuda.synchronize(dev)
