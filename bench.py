@@ -191,7 +191,9 @@ def accuracy_report(workload):
             d = json.load(fh)
     except (OSError, ValueError):
         return None
-    if d.get("source_hash") != source_hash():
+    from paper_2401_06003_gb300.build import RENDER_PATH_FILES
+
+    if d.get("source_hash") != source_hash(RENDER_PATH_FILES):
         return None
     return d
 

@@ -69,6 +69,11 @@ def source_hash(files=None) -> str:
     return h.hexdigest()[:16]
 
 
+# the sources of the render path (projection, binning, blend, backward and their
+# ABI): an accuracy report of the path is valid while these are unchanged
+RENDER_PATH_FILES = ("abi.cu", "bin.cu", "blend.cu", "common.cuh")
+
+
 def up_to_date(lib: str = LIB) -> bool:
     if not os.path.exists(lib):
         return False

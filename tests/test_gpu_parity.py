@@ -309,9 +309,9 @@ def test_ground10m_4k_bf16_crops():
     o_f32 = _oracle(sc, pixels=pix)
     ref_f = o_f32.render()
     assert_close_scaled(out["pyramid"][rows], ref_f["pyramid"], BF16_RTOL, name="4k bf16 vs oracle(f32)")
-    from paper_2401_06003_gb300.build import source_hash
+    from paper_2401_06003_gb300.build import RENDER_PATH_FILES, source_hash
 
-    report = {"workload": "ground10m_4k_bf16", "source_hash": source_hash(), "crops": "8 seeded 64x64 crops of layer 0 and the coarser pixels "
+    report = {"workload": "ground10m_4k_bf16", "source_hash": source_hash(RENDER_PATH_FILES), "crops": "8 seeded 64x64 crops of layer 0 and the coarser pixels "
               "above them", "pixels": int(rows.size)}
     report["pyramid"] = {"vs_oracle_bf16_values": _error_stats(out["pyramid"][rows], ref_bf["pyramid"]),
                          "vs_oracle_f32_values": _error_stats(out["pyramid"][rows], ref_f["pyramid"])}
