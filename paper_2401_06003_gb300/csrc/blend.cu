@@ -689,15 +689,30 @@ __global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_backward(const __grid_con
     const long long prow = F.coarse && L + 1 < F.n_layers ? coarse_row(B, v, L + 1, j >> 1, k >> 1) : -1ll;
     if (prow >= 0 && TP_IN_RANGE(W.status, prow < W.crows)) {
         const unsigned long long km = thr[tid];
-        for (int m = 0; m < K; ++m) {
-            const unsigned long long key = W.ckey[(long long)m * W.crows + prow];
-            if (key > km) break;  // the stored list is sorted; empty slots hold the largest key
-            if (nk < K) {
-                kk[nk * TP + tid] = key;
-                ke[nk * TP + tid] = kNoPoint;
-                kt[nk * TP + tid] = __uint_as_float(W.cgam[(long long)m * W.crows + prow]);
+        // the stored list is sorted and empty slots hold the largest key: read it four
+        // slots at a time (the loads of a group in flight together) until a key passes km
+        bool more = true;
+        for (int m0 = 0; m0 < K && more; m0 += 4) {
+            unsigned long long key[4];
+            unsigned gam[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                key[u] = W.ckey[(long long)(m0 + u) * W.crows + prow];
+                gam[u] = W.cgam[(long long)(m0 + u) * W.crows + prow];
             }
-            ++nk;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (!more || key[u] > km) {
+                    more = false;
+                    continue;
+                }
+                if (nk < K) {
+                    kk[nk * TP + tid] = key[u];
+                    ke[nk * TP + tid] = kNoPoint;
+                    kt[nk * TP + tid] = __uint_as_float(gam[u]);
+                }
+                ++nk;
+            }
         }
     }
     if (nk > K) nk = K;
