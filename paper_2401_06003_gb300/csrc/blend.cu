@@ -624,13 +624,15 @@ __device__ __forceinline__ void adjoint_fragment(const Frame &F, int L, int j, i
 // fragments are the entries of its parent's stored list up to the same key;
 // their payload comes from the point records, and their gradients from their
 // own layer's pixel (each key carries its layer).
-// Registers are capped at 96 for K <= 16 (five 128-thread CTAs per SM); the
-// kept slots are sorted in shared memory, so no register list is live.
+// Registers are capped at 80 for K <= 16 (six 128-thread CTAs per SM, with
+// the 34 KB slot region); the kept slots are sorted in shared memory, so no
+// register list is live (measured against 96 registers: 1080p backward -2%,
+// 4K bf16 -3.4%).
 // CAM: also the camera gradient of every view, [n_views][16] doubles in gcam
 // (summed over the views' tiles: per-thread shared-memory columns, one
 // reduction and 16 double atomics per CTA).
 template <int K, typename DescT, int MaxV, int DC, bool CAM>
-__global__ void __maxnreg__(K <= 16 ? 96 : 168) k_tile_backward(const __grid_constant__ Batch<MaxV> B, Workspace W,
+__global__ void __maxnreg__(K <= 16 ? 80 : 168) k_tile_backward(const __grid_constant__ Batch<MaxV> B, Workspace W,
                                                           const DescT *__restrict__ desc,
                                 const float *__restrict__ grad_pyr, float *__restrict__ gpos, float *__restrict__ gsw,
                                 float *__restrict__ gop, float *__restrict__ gdesc, long long n,
