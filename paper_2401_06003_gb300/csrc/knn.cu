@@ -9,8 +9,10 @@
 //      hash of their cell -- its Morton code modulo the table size, so that
 //      neighbouring cells sit in neighbouring table entries -- (count,
 //      three-phase scan, fill), the sorted copy holding (x, y, z, index);
-//   3. a ring search per point: rings r = 0, 1, 2, ... of cells around the
-//      point's cell; every unvisited point is farther than r c_m, so the
+//   3. a ring search per point (level 0: one thread per point; later levels,
+//      whose few points meet the densest cells, one warp per point): rings
+//      r = 0, 1, 2, ... of cells around the point's cell; every unvisited
+//      point is farther than r c_m, so the
 //      search stops once it holds k neighbours within r c_m.  A point not
 //      settled within kRingsPerLevel rings moves to the next, coarser level
 //      (dense regions settle on fine grids, sparse ones climb); the last
@@ -366,6 +368,111 @@ __device__ bool search_point(const KnnWs &W, int level, bool last, unsigned self
     return false;
 }
 
+// The k smallest of the union of the lanes' lists (each ascending), the same
+// in every lane: k rounds of a warp minimum, the lane that held it moving on.
+// Squared distances are >= +0, so their bits order like their values.
+__device__ __forceinline__ void warp_best(const Best &b, float out[kKnnK], int &cnt)
+{
+    const int lane = threadIdx.x & 31;
+    int p = 0;
+    cnt = 0;
+#pragma unroll
+    for (int r = 0; r < kKnnK; ++r) {
+        float mine = INFINITY;
+#pragma unroll
+        for (int q = 0; q < kKnnK; ++q) mine = p == q ? b.d[q] : mine;
+        const unsigned mu = __float_as_uint(mine);
+        const unsigned m = __reduce_min_sync(0xffffffffu, mu);
+        out[r] = __uint_as_float(m);
+        cnt += m != __float_as_uint(INFINITY) ? 1 : 0;
+        const unsigned who = __ballot_sync(0xffffffffu, mu == m);
+        if (lane == __ffs(who) - 1 && m != __float_as_uint(INFINITY)) ++p;
+    }
+}
+
+// search_point for one point by a whole warp: the rings and cells are the
+// same for every lane, each lane takes every 32nd point of a cell, and the
+// lanes' lists are merged at the end of every ring (for the stop test and
+// the pruning bound).  For the few points left to the coarser levels, whose
+// cells can hold thousands of points.  Same result as search_point.
+__device__ bool search_point_warp(const KnnWs &W, int level, bool last, unsigned self, float x, float y, float z,
+                                  float &bound, float *__restrict__ size_w)
+{
+    const KnnHdr *hdr = W.hdr;
+    const int lane = threadIdx.x & 31;
+    const float c = level_cell(hdr, level), inv_c = 1.0f / c;
+    const int cx = cell_of(x, hdr->lo[0], inv_c), cy = cell_of(y, hdr->lo[1], inv_c), cz = cell_of(z, hdr->lo[2], inv_c);
+    const unsigned nf = hdr->n_finite;
+    const int want = (int)min((unsigned)kKnnK, nf > 0 ? nf - 1 : 0u);
+    const int r_all = (int)(hdr->extent * inv_c) + 2;
+    const int r_max = last ? r_all : min(kRingsPerLevel, r_all);
+    Best b;
+    b.clear();
+    float merged[kKnnK];
+    int n_merged = 0;
+    float prune = bound;  // uniform: the carried bound, then the merged 4th distance
+    for (int r = 0; r <= r_max; ++r) {
+        for (int dz = -r; dz <= r; ++dz) {
+            for (int dy = -r; dy <= r; ++dy) {
+                const bool face = dz == -r || dz == r || dy == -r || dy == r;
+                for (int dx = -r; dx <= r; dx += face ? 1 : 2 * r) {
+                    const int ix = cx + dx, iy = cy + dy, iz = cz + dz;
+                    if (r > 0 && cell_dist2(hdr, c, ix, iy, iz, x, y, z) > prune) continue;
+                    const unsigned h = cell_hash(ix, iy, iz, W.T);
+                    const unsigned e0 = W.start[h], e1 = W.start[h + 1];
+                    for (unsigned q = e0 + lane; q < e1; q += 32) {
+                        const float4 p = W.spos[q];
+                        if (__float_as_uint(p.w) == self) continue;
+                        if (cell_of(p.x, hdr->lo[0], inv_c) != ix || cell_of(p.y, hdr->lo[1], inv_c) != iy ||
+                            cell_of(p.z, hdr->lo[2], inv_c) != iz)
+                            continue;  // another cell with the same hash
+                        const float ex = p.x - x, ey = p.y - y, ez = p.z - z;
+                        b.insert(ex * ex + ey * ey + ez * ez);
+                    }
+                    if (r == 0) break;
+                }
+            }
+        }
+        warp_best(b, merged, n_merged);
+        if (n_merged >= kKnnK) prune = fminf(bound, merged[kKnnK - 1]);
+        const float reach = (float)r * c * 0.98f;  // as in search_point
+        const bool done = r >= r_all || (n_merged >= want && (want == 0 || merged[want - 1] <= reach * reach));
+        if (done) {
+            if (lane == 0) {
+                float s = 0.0f;
+                for (int q = 0; q < want; ++q) s += sqrtf(merged[q]);
+                size_w[self] = want > 0 ? s / (float)want : 0.0f;
+            }
+            return true;
+        }
+    }
+    if (n_merged >= kKnnK) bound = fminf(bound, merged[kKnnK - 1]);
+    return false;
+}
+
+// Levels >= 1: one warp per point left unsettled.
+__global__ void __launch_bounds__(kKnnBlock) k_knn_query_warp(const float *__restrict__ pos, KnnWs W, int level,
+                                                              int last, float *__restrict__ size_w)
+{
+    KnnHdr *hdr = W.hdr;
+    const unsigned todo = hdr->n_open[(level - 1) & 1];
+    const unsigned *in = W.open[(level - 1) & 1];
+    const float *in_bound = W.bound[(level - 1) & 1];
+    unsigned *out = W.open[level & 1];
+    float *out_bound = W.bound[level & 1];
+    const unsigned warps = gridDim.x * (blockDim.x >> 5);
+    for (unsigned t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < todo; t += warps) {
+        const unsigned i = in[t];
+        float bound = in_bound[t];
+        const float x = pos[3 * (long long)i], y = pos[3 * (long long)i + 1], z = pos[3 * (long long)i + 2];
+        if (!search_point_warp(W, level, last != 0, i, x, y, z, bound, size_w) && (threadIdx.x & 31) == 0) {
+            const unsigned slot = atomicAdd(&hdr->n_open[level & 1], 1u);
+            out[slot] = i;
+            out_bound[slot] = bound;
+        }
+    }
+}
+
 // Level 0 visits the points in their sorted order (neighbouring threads search
 // neighbouring cells); later levels take the list of points left unsettled.
 __global__ void __launch_bounds__(kKnnBlock) k_knn_query(const float *__restrict__ pos, KnnWs W, int level, int last,
@@ -482,7 +589,10 @@ tp_status tp_init_point_sizes(int64_t n, const float *pos, float *size_w, void *
         k_scan_add<<<(L.T + 255) / 256, 256, 0, s>>>(W.start, W.bsum, L.T);
         if (cudaMemsetAsync(W.count, 0, 4 * (size_t)L.T, s) != cudaSuccess) return TP_ERR_CUDA;
         k_knn_fill<<<grid_pts, kKnnBlock, 0, s>>>(n, pos, W, level);
-        k_knn_query<<<kKnnGrid, kKnnBlock, 0, s>>>(pos, W, level, level == kKnnLevels - 1, size_w);
+        if (level == 0)
+            k_knn_query<<<kKnnGrid, kKnnBlock, 0, s>>>(pos, W, level, 0, size_w);
+        else
+            k_knn_query_warp<<<kKnnGrid, kKnnBlock, 0, s>>>(pos, W, level, level == kKnnLevels - 1, size_w);
         if (cudaGetLastError() != cudaSuccess) return TP_ERR_CUDA;
     }
     return TP_OK;
