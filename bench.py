@@ -54,6 +54,8 @@ def parse_args():
                     help="skip the camera-adjoint, pyramid-merge and point-size timings (profiling the step alone)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-other-workloads", action="store_true",
+                    help="skip the summaries of the batched 16-view and 4K bf16 workloads in the default line")
     return ap.parse_args()
 
 
@@ -645,6 +647,9 @@ def run_ours(args):
             "e2e": e2e,
             "gpu_launches": KERNELS_PER_STEP * args.steps, "clocks": clk, "device_flags": flags,
         }
+        if world == 1 and not args.no_extras and not args.no_other_workloads and args.workload == "ground6m_1080p" \
+                and not args.points:
+            line["other_workloads"] = other_workloads(args)
         print(json.dumps(line), flush=True)
 
 
@@ -923,6 +928,36 @@ def run_reference(args):
         "e2e": {"value": round(value, 4), "unit": "Mpoints/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def other_workloads(args):
+    """One-line summaries of the batched 16-view workload and the 4K bf16 workload,
+    each run as its own bench process after the headline has been timed (the same
+    timing rules; their full lines come from --workload)."""
+    out = {}
+    for w in ("ground6m_orbit16", "ground10m_4k_bf16"):
+        cmd = [sys.executable, os.path.abspath(__file__), "--workload", w, "--steps", str(args.steps),
+               "--warmup", str(args.warmup), "--no-cpu-baseline", "--no-e2e"]
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=600)
+            d = json.loads(r.stdout.strip().splitlines()[-1])
+        except (subprocess.SubprocessError, ValueError, IndexError) as exc:
+            out[w] = {"error": str(exc)[:200]}
+            continue
+        keep = ("metric", "value", "unit", "ms_per_step", "forward_ms", "batch_step_ms", "per_view_in_batch_ms",
+                "single_view_p50_ms", "single_view_p99_ms", "f32_form", "clocks", "device_flags")
+        s = {k: d[k] for k in keep if k in d}
+        if d.get("roofline"):
+            s["roofline_frac"] = d["roofline"].get("frac")
+            s["step_frac"] = d["roofline"].get("step", {}).get("frac")
+        acc = d.get("accuracy")
+        if acc:  # max relative errors on the crops against the float64 oracle
+            s["accuracy_max_rel"] = {q: {k: acc[q][k]["max_rel"] for k in ("vs_oracle_bf16_values",
+                                                                            "vs_oracle_f32_values")}
+                                     for q in ("pyramid", "grad_pos", "grad_size_w", "grad_opacity", "grad_desc")
+                                     if q in acc}
+        out[w] = s
+    return out
 
 
 def main():
