@@ -223,6 +223,11 @@ struct TopK {
     }
 };
 
+// Light tiles: up to kDirectEntries tile-list entries per thread go straight
+// into per-pixel buckets of up to kDirectCap keys.
+constexpr int kDirectEntries = 1;
+constexpr int kDirectCap = 16;
+
 // Builds the kept list of the thread's pixel (thread t owns pixel t of the
 // tile, t < tile_px); returns the kept count.  With count_all, *nfrag gets
 // the pixel's number of candidate fragments in the tile's own list.  A
@@ -259,6 +264,34 @@ __device__ int build_topk(const Frame &F, const Workspace &W, int tile, const Ti
     unsigned nfr = 0;
     const bool multi = !count_all && end - beg > (unsigned)F.chunk;
     __syncthreads();
+    // A light tile (at most kDirectEntries entries per thread) skips the count and scan:
+    // each pixel gets a fixed bucket of dcap slots and the entries append to
+    // it directly; if any pixel overflows its bucket the tile takes the
+    // general path below.
+    const int dcap = min(kDirectCap, 4 * F.chunk / NT);
+    if (end - beg <= (unsigned)(kDirectEntries * NT) && dcap > 0) {
+        for (unsigned e = beg + tid; e < end; e += NT) {
+            const unsigned long long key = W.bucket_key[e];
+            entry_taps(F, g, W.bucket_pay[e], [&](int px) {
+                if (!TP_IN_RANGE(W.status, px >= 0 && px < TP)) return;
+                const unsigned q = atomicAdd(S.cnt + px, 1u);
+                if (q < (unsigned)dcap) S.ck[px * dcap + q] = key;
+            });
+        }
+        __syncthreads();
+        const unsigned my = S.cnt[tid];
+        if (!__syncthreads_or(my > (unsigned)dcap)) {
+            const int lim = min(K, __reduce_max_sync(0xffffffffu, owner ? top.n : 0) +
+                                       (int)__reduce_max_sync(0xffffffffu, owner ? my : 0u));
+            if (owner)
+                for (unsigned q = 0; q < my; ++q) top.insert_bounded(S.ck[tid * dcap + q], lim);
+            *nfrag = my;
+            __syncthreads();  // the caller's epilogue reuses the shared memory
+            return top.n;
+        }
+        S.cnt[tid] = 0u;  // a bucket overflowed: the general path
+        __syncthreads();
+    }
     for (unsigned c0 = beg; c0 < end; c0 += (unsigned)F.chunk) {
         const unsigned c1 = min(end, c0 + (unsigned)F.chunk);
         if (multi) {
