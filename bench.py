@@ -53,6 +53,8 @@ def parse_args():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the camera-adjoint, pyramid-merge and point-size timings (profiling the step alone)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--copy-streams", type=int, default=1,
+                    help="copy streams the end-to-end upload and download are split over")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-other-workloads", action="store_true",
                     help="skip the summaries of the batched 16-view and 4K bf16 workloads in the default line")
@@ -410,42 +412,64 @@ def run_ours(args):
         # the step's result read back: the loss <G, pyramid> whose gradient is the
         # upstream gradient G (the point gradients stay on the device, as for an
         # optimizer step); a second figure also downloads every gradient
-        d_loss = torch.empty((), dtype=torch.float32, device=dev)
+        d_loss = [torch.empty((), dtype=torch.float32, device=dev) for _ in range(2)]
         h_loss = [torch.empty((), dtype=torch.float32).pin_memory() for _ in range(2)]
         h2d = sum(t.numel() * t.element_size() for t in h_in)
         d2h_grads = sum(t.numel() * t.element_size() for t in h_out[0])
-        s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        # each tensor's copy is cut into contiguous pieces, one per copy stream
+        # (one copy stream alone does not reach the host link's bandwidth)
+        n_cs = max(1, args.copy_streams)
+        s_in = [torch.cuda.Stream(dev) for _ in range(n_cs)]
+        s_out = [torch.cuda.Stream(dev) for _ in range(n_cs)]
         computed = [torch.cuda.Event() for _ in range(2)]
-        downloaded = [torch.cuda.Event() for _ in range(2)]
-        uploaded = [torch.cuda.Event() for _ in range(2)]
+        downloaded = [[torch.cuda.Event() for _ in range(n_cs)] for _ in range(2)]
+        uploaded = [[torch.cuda.Event() for _ in range(n_cs)] for _ in range(2)]
+
+        def pieces(dst, src):
+            """(stream index, dst piece, src piece) over the copy streams."""
+            a_, b_ = dst.view(-1), src.view(-1)
+            n_ = a_.numel()
+            step = -(-n_ // n_cs)
+            step = -(-step // 1024) * 1024
+            return [(j, a_[j * step:min(n_, (j + 1) * step)], b_[j * step:min(n_, (j + 1) * step)])
+                    for j in range(n_cs) if j * step < n_]
 
         def pipeline(steps, download_grads):
             for k in range(steps):
                 b = k % 2
                 if k >= 2:
-                    s_in.wait_event(computed[b])      # step k-2 no longer reads these inputs
-                    stream.wait_event(downloaded[b])  # its results are on the host
-                with torch.cuda.stream(s_in):
-                    for d_, h_ in zip(d_in[b], h_in):
-                        d_.copy_(h_, non_blocking=True)
-                    uploaded[b].record(s_in)
-                stream.wait_event(uploaded[b])
+                    for s_ in s_in:
+                        s_.wait_event(computed[b])    # step k-2 no longer reads these inputs
+                    for ev in downloaded[b]:
+                        stream.wait_event(ev)          # its results are on the host
+                for d_, h_ in zip(d_in[b], h_in):
+                    for j, dp, hp in pieces(d_, h_):
+                        with torch.cuda.stream(s_in[j]):
+                            dp.copy_(hp, non_blocking=True)
+                for j, s_ in enumerate(s_in):
+                    uploaded[b][j].record(s_)
+                    stream.wait_event(uploaded[b][j])
                 pb, swb, opb, db = d_in[b]
                 r.project(pb, swb, ws, records=rec)
                 r.splat_forward(rec, opb, ws)
                 _, kept_b, nk_b, _, _ = r.blend(rec, opb, db, ws, store_lists=store, pyramid=pyr)
-                torch.dot(pyr.view(-1), G.view(-1), out=d_loss)
+                torch.dot(pyr.view(-1), G.view(-1), out=d_loss[b])
                 r.splat_backward(rec, opb, db, G, ws, kept_b if store else None, nk_b if store else None,
                                  grads=tuple(d_gr[b]))
                 computed[b].record(stream)
-                s_out.wait_event(computed[b])
-                with torch.cuda.stream(s_out):
-                    h_loss[b].copy_(d_loss, non_blocking=True)
-                    if download_grads:
-                        for h_, g_ in zip(h_out[b], [g for g in d_gr[b] if g is not None]):
-                            h_.copy_(g_, non_blocking=True)
-                    downloaded[b].record(s_out)
-            stream.wait_stream(s_out)
+                for s_ in s_out:
+                    s_.wait_event(computed[b])
+                with torch.cuda.stream(s_out[0]):
+                    h_loss[b].copy_(d_loss[b], non_blocking=True)
+                if download_grads:
+                    for h_, g_ in zip(h_out[b], [g for g in d_gr[b] if g is not None]):
+                        for j, hp, gp in pieces(h_, g_):
+                            with torch.cuda.stream(s_out[j]):
+                                hp.copy_(gp, non_blocking=True)
+                for j, s_ in enumerate(s_out):
+                    downloaded[b][j].record(s_)
+            for s_ in s_out:
+                stream.wait_stream(s_)
 
         def timed_pipeline(download_grads):
             pipeline(min(args.warmup, 3), download_grads)
@@ -454,20 +478,48 @@ def run_ours(args):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            s_in.wait_stream(stream)
+            for s_ in s_in:
+                s_.wait_stream(stream)
             pipeline(args.steps, download_grads)
             e1.record(stream)
             torch.cuda.synchronize(dev)
             barrier(world, dev)
             return max_over_ranks(e0.elapsed_time(e1), world, dev) / args.steps
 
+        def upload_alone(reps=10):
+            """The step's host->device copies alone (no kernels): the bound the
+            host link puts on the end-to-end step."""
+            def once():
+                for d_, h_ in zip(d_in[1], h_in):
+                    for j, dp, hp in pieces(d_, h_):
+                        with torch.cuda.stream(s_in[j]):
+                            dp.copy_(hp, non_blocking=True)
+            once()
+            torch.cuda.synchronize(dev)
+            u0 = torch.cuda.Event(enable_timing=True)
+            u1 = torch.cuda.Event(enable_timing=True)
+            u0.record(stream)
+            for s_ in s_in:
+                s_.wait_stream(stream)
+            for _ in range(reps):
+                once()
+            for s_ in s_in:
+                stream.wait_stream(s_)
+            u1.record(stream)
+            torch.cuda.synchronize(dev)
+            return u0.elapsed_time(u1) / reps
+
         e2e_ms = timed_pipeline(False)
         e2e_grads_ms = timed_pipeline(True)
+        up_ms = upload_alone()
         e2e = {"value": round(N * world / (e2e_ms * 1e-3) / 1e6, 3), "unit": "Mpoints/s",
                "ms_per_step": round(e2e_ms, 4), "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(h_loss[0].numel() * h_loss[0].element_size()),
                "result": "the loss <G, pyramid> (G is its gradient); point gradients stay on the device",
-               "overlap": "double-buffered: uploads on a copy stream overlap the kernels",
+               "overlap": "double-buffered: uploads on %d copy stream(s) overlap the kernels" % n_cs,
+               "upload_alone_ms": round(up_ms, 4),
+               "upload_gbs": round(h2d / (up_ms * 1e-3) / 1e9, 1),
+               "frac_of_upload_bound": round(up_ms / e2e_ms, 3),
                "with_gradients_downloaded": {
                    "value": round(N * world / (e2e_grads_ms * 1e-3) / 1e6, 3), "ms_per_step": round(e2e_grads_ms, 4),
                    "d2h_bytes_per_step": int(d2h_grads + 4)}}

@@ -397,9 +397,10 @@ __device__ __forceinline__ DescGroup<DescT> load_group(const DescT *__restrict__
 
 // STATS: the frame's candidate counts are asked for (n_frag); a separate
 // instantiation, so the plain blend carries none of that state.  Registers
-// are capped at 96 for K <= 16 so that five 128-thread CTAs fit on an SM
-// (the uncapped build of some instantiations takes 104 and fits four: the
-// 4K bf16 blend was 14% slower); K = 32 needs its registers for the list.
+// are capped at 80 for K <= 16 so that six 128-thread CTAs fit on an SM
+// (the keys-only list and its bounded chains fit without spilling; uncapped
+// builds of some instantiations take 104 and fit four, which made the 4K bf16
+// blend 14% slower); K = 32 needs its registers for the list.
 // layer < 0: every tile of the batch; else the tiles of that layer (the
 // coarse-to-fine launches of coarse-layer inclusion).
 template <int K, typename DescT, int MaxV, bool STATS>
