@@ -8,9 +8,12 @@
 // count and fill passes make 1-2 global atomics per point instead of 4-8,
 // and the per-pixel lists are formed later in shared memory by the blend
 // kernel (blend.cu), which reads each tile's points with coalesced loads.
-// Each tile counter is split into kCopies copies (point i uses copy
-// i % kCopies) so that the thousands of points of a dense tile do not queue
-// on one address; k_tile_totals folds the copies back together.
+// Each tile counter is split into kCopies copies (the points of warp w use
+// copy w % kCopies) so that the thousands of points of a dense tile do not
+// queue on one address; k_tile_totals folds the copies back together.  The
+// lanes of a warp that touch the same tile together make one atomic for the
+// group, so a group's entries are consecutive in the tile's list and its
+// stores coalesce.
 #include "common.cuh"
 
 namespace tpk {
@@ -35,6 +38,15 @@ __device__ __forceinline__ void for_each_tile(const Frame &F, const float4 &r, F
             for (int a = x0; a <= x1; ++a) fn(base + b * tpr + a, L);
     }
 }
+
+// The lanes of the calling warp that are here together and hold the same
+// tile t: one group, whose lowest lane makes the group's atomic.
+__device__ __forceinline__ unsigned tile_group(int t) { return __match_any_sync(__activemask(), t); }
+
+// Copy of the counters point i uses: the same for every lane of its warp (the
+// grid's threads are whole warps of consecutive i), so a group's atomic goes
+// to the copy each of its points would use.
+__device__ __forceinline__ unsigned point_copy(long long i) { return (unsigned)((i >> 5) & (kCopies - 1)); }
 
 // Collect: project, cull, write the record and count (point, tile) pairs.
 // blockIdx.y is the view; view v writes records rec[v n + i] and counts into
@@ -61,9 +73,12 @@ __global__ void __launch_bounds__(kBlock) k_project_count(const __grid_constant_
             continue;
         }
         rec[i] = r;
-        const unsigned c = (unsigned)(i & (kCopies - 1));
+        const unsigned c = point_copy(i);
+        const int lane = threadIdx.x & 31;
         for_each_tile(F, r, [&](int t, int) {
-            if (TP_IN_RANGE(W.status, t >= 0 && t < F.n_tiles)) atomicAdd(count + (size_t)t * kCopies + c, 1u);
+            if (!TP_IN_RANGE(W.status, t >= 0 && t < F.n_tiles)) return;
+            const unsigned grp = tile_group(t);
+            if (lane == __ffs(grp) - 1) atomicAdd(count + (size_t)t * kCopies + c, (unsigned)__popc(grp));
         });
     }
 }
@@ -172,11 +187,18 @@ __global__ void __launch_bounds__(kBlock) k_fill(const __grid_constant__ Batch<M
         const float4 r = rec[i];
         if (!(r.z > 0.0f)) continue;  // culled
         const float4 pay = make_float4(r.x, r.y, r.w, __ldg(opacity + i));
-        const unsigned c = (unsigned)(i & (kCopies - 1));
+        const unsigned c = point_copy(i);
+        const int lane = threadIdx.x & 31;
         for_each_tile(F, r, [&](int t, int L) {
             if (!TP_IN_RANGE(W.status, t >= 0 && t < F.n_tiles)) return;
             const unsigned long long key = frag_key(r.z, (unsigned)i, L);
-            const unsigned e = tile_off[t] + atomicAdd(cursor + (size_t)t * kCopies + c, 1u);
+            // the group takes consecutive slots of its copy, in lane order
+            const unsigned grp = tile_group(t);
+            const int lead = __ffs(grp) - 1;
+            unsigned base = 0u;
+            if (lane == lead) base = atomicAdd(cursor + (size_t)t * kCopies + c, (unsigned)__popc(grp));
+            const unsigned e =
+                tile_off[t] + __shfl_sync(grp, base, lead) + (unsigned)__popc(grp & ((1u << lane) - 1u));
             if (e < W.capacity) {
                 W.bucket_key[e] = key;
                 W.bucket_pay[e] = pay;

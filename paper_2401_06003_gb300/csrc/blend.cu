@@ -292,26 +292,46 @@ __device__ int build_topk(const Frame &F, const Workspace &W, int tile, const Ti
         S.cnt[tid] = 0u;  // a bucket overflowed: the general path
         __syncthreads();
     }
-    for (unsigned c0 = beg; c0 < end; c0 += (unsigned)F.chunk) {
-        const unsigned c1 = min(end, c0 + (unsigned)F.chunk);
+    // A multi-chunk tile's chunks are made of 32-entry blocks of its list taken
+    // round-robin (chunk k: blocks k, k + nch, ...), so that every chunk samples
+    // the whole list: the fill writes the points of one warp as one run, and
+    // contiguous chunks would give a pixel most of its fragments in one chunk,
+    // before any threshold of it exists.  Each chunk holds at most
+    // floor(chunk / 32) blocks, so at most F.chunk entries.
+    const unsigned nb = (end - beg + 31u) / 32u;
+    const unsigned bpc = (unsigned)F.chunk / 32u;
+    const unsigned nch = multi ? (nb + bpc - 1u) / bpc : (end - beg + (unsigned)F.chunk - 1u) / (unsigned)F.chunk;
+    for (unsigned ch = 0; ch < nch; ++ch) {
+        const unsigned c0 = beg + ch * (unsigned)F.chunk, c1 = min(end, c0 + (unsigned)F.chunk);
+        auto each_entry = [&](auto &&fn) {
+            if (multi) {
+                for (unsigned bb = ch + nch * (unsigned)(tid >> 5); bb < nb; bb += nch * (unsigned)(NT >> 5)) {
+                    const unsigned e = beg + bb * 32u + (unsigned)(tid & 31);
+                    if (e < end) fn(e);
+                }
+            } else {
+                for (unsigned e = c0 + tid; e < c1; e += NT) fn(e);
+            }
+        };
         if (multi) {
-            for (unsigned e = c0 + tid; e < c1; e += NT) {
+            each_entry([&](unsigned e) {
                 const unsigned long long key = W.bucket_key[e];
                 entry_taps(F, g, W.bucket_pay[e], [&](int px) {
                     if (TP_IN_RANGE(W.status, px >= 0 && px < TP) && key < S.thr[px]) atomicAdd(S.cnt + px, 1u);
                 });
-            }
+            });
         } else {
-            for (unsigned e = c0 + tid; e < c1; e += NT)
+            each_entry([&](unsigned e) {
                 entry_taps(F, g, W.bucket_pay[e], [&](int px) {
                     if (TP_IN_RANGE(W.status, px >= 0 && px < TP)) atomicAdd(S.cnt + px, 1u);
                 });
+            });
         }
         __syncthreads();
         const unsigned my = S.cnt[tid];
         S.off[tid] = block_exclusive_scan(my, S.wsum);
         __syncthreads();
-        for (unsigned e = c0 + tid; e < c1; e += NT) {
+        each_entry([&](unsigned e) {
             const unsigned long long key = W.bucket_key[e];
             entry_taps(F, g, W.bucket_pay[e], [&](int px) {
                 if (!TP_IN_RANGE(W.status, px >= 0 && px < TP)) return;
@@ -320,7 +340,7 @@ __device__ int build_topk(const Frame &F, const Workspace &W, int tile, const Ti
                     if (TP_IN_RANGE(W.status, q < 4u * (unsigned)F.chunk)) S.ck[q] = key;
                 }
             });
-        }
+        });
         __syncthreads();
         // every list of the warp stays below lim slots during this chunk's merge
         const int lim = min(K, __reduce_max_sync(0xffffffffu, owner ? top.n : 0) +

@@ -108,9 +108,10 @@ __device__ __forceinline__ int view_of_pixel(const Batch<MaxV> &B, long long pix
 }
 
 // Device pointers into the caller's workspace.
-// Every tile counter exists in kCopies copies; point i uses copy i % kCopies.
-// Hot tiles (thousands of points near the horizon) would otherwise serialise
-// their atomics on one address.
+// Every tile counter exists in kCopies copies; point i uses copy
+// (i / 32) % kCopies, the same for the 32 points of a warp.  Hot tiles
+// (thousands of points near the horizon) would otherwise serialise their
+// atomics on one address.
 constexpr int kCopies = 32;
 
 struct Workspace {
